@@ -1,0 +1,164 @@
+/*
+ * polaris.h — C ABI of the GB300-native PolariS spectrometer hot path.
+ *
+ * The operation (arXiv:1412.1256, Sec. 2 and the Fig. 2 caption): the GPU takes
+ * the quantised voltage samples of each IF stream, translates the integer codes
+ * to floats, cuts the stream into segments, transforms each segment with an FFT,
+ * forms the power spectra <XX*>, <YY*> and the cross power spectrum <XY*>
+ * (Fig. 1 caption; Table 1: 4 real autocorrelations, 2 complex cross
+ * correlations) and integrates them; the full-Stokes spectra I, Q, U, V follow
+ * from Eq. (2) (Sec. 2.1).  Every step runs in hand-written CUDA kernels for
+ * sm_103a; this header has no CUDA or PyTorch types.
+ *
+ * Conventions (readings where the paper is silent):
+ *   - Input: one planar stream of little-endian uint32 words per IF; sample j of
+ *     a word sits in bits [j*bits, (j+1)*bits).  bits < 8: code c has level
+ *     2c - (2^bits - 1) (2-bit: -3, -1, +1, +3); bits = 8: two's-complement int8.
+ *   - Segment s covers stream samples [s*hop, s*hop + n_fft); only whole segments
+ *     are transformed; the remainder is carried to the next feed.
+ *   - Transform: unnormalised forward DFT, X_k = sum_n w[n] y[n] e^{-2 pi i n k/N},
+ *     bins k = 0 .. N/2 (N/2 + 1 bins; DC and Nyquist included).
+ *   - Integration: sums over segments (not means); autos A_i[k] = sum |X_i,k|^2,
+ *     cross C_p[k] = sum X_a,k conj(X_b,k) for pair p = (a, b).
+ *   - Stokes, linear feeds: Eq. (2) with x = XX/|Ga|^2, c = XY/(Ga conj(Gb)),
+ *     y = YY/|Gb|^2, i.e. I = (x+y)/2, Q = [cos2psi (x-y) - sin2psi 2Re c]/2,
+ *     U = [sin2psi (x-y) + cos2psi 2Re c]/2, V = Im c.
+ *     Circular feeds (R, L): I = (RR+LL)/2, V = (RR-LL)/2, Q + iU = e^{2i psi} R conj(L).
+ *
+ * Threading: a handle is not thread-safe.  Errors never cross the ABI as
+ * exceptions: every call returns a status; spectrometer_last_error() gives text.
+ * A CUDA error inside a call is sticky: the handle answers POLARIS_ESTATE to
+ * every later call except destroy and last_error.
+ */
+#ifndef POLARIS_H
+#define POLARIS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+enum {
+  POLARIS_OK = 0,
+  POLARIS_EINVAL = -1,   /* bad argument; the call had no effect            */
+  POLARIS_ENOMEM = -2,   /* device or pinned-host allocation failed          */
+  POLARIS_ECUDA = -3,    /* a CUDA call failed; the handle is now unusable   */
+  POLARIS_ESTATE = -4,   /* wrong state (e.g. integrate with zero segments,
+                            or a handle after a CUDA error)                  */
+  POLARIS_ETIMEOUT = -5  /* reserved for bounded device-side waits           */
+};
+
+/* window kinds (Sec. 3.1: rectangular online; Sec. 5: others possible) */
+enum { POLARIS_WIN_RECT = 0, POLARIS_WIN_HANN = 1, POLARIS_WIN_CUSTOM = 2 };
+
+/* feed types for Stokes */
+enum { POLARIS_FEED_LINEAR = 0, POLARIS_FEED_CIRCULAR = 1 };
+
+typedef struct polaris_spec polaris_spec; /* opaque, library-owned */
+
+/* Spectrometer configuration (Table 1: number of IFs, quantisation, channels).
+ *   n_if        1..8 IF streams.
+ *   bits        1, 2, 4 or 8 bits per sample.
+ *   n_fft       segment length N, a power of two in [16, 524288]; N/2+1 bins.
+ *   hop         segment spacing in samples, 0 < hop <= n_fft, a multiple of
+ *               32/bits (0 means hop = n_fft; hop = n_fft/2 is the 50% overlap
+ *               of Sec. 3.1).
+ *   window      POLARIS_WIN_*; taps: n_fft float taps for POLARIS_WIN_CUSTOM
+ *               (copied at create; ignored otherwise).  Hann is periodic:
+ *               0.5 - 0.5 cos(2 pi n / N).
+ *   n_pair      number of (X, Y) correlation pairs; pairs: 2*n_pair IF indices
+ *               (a, b), each IF in at most one pair.  pairs == NULL selects the
+ *               default: IF i with IF i + n_if/2 for even n_if (Table 1 order
+ *               X0, X1, Y0, Y1 gives (X0, Y0), (X1, Y1)); none for odd n_if.
+ *   accum_fp64  1: integration accumulators in FP64 (per-launch partial sums in
+ *               FP32); 0: FP32.
+ *   device      CUDA device ordinal.
+ *   max_batch_segments  segments processed per kernel pass (bounds the device
+ *               scratch: max_batch_segments * n_fft * 8 bytes per pair);
+ *               0 selects a default that keeps the scratch inside L2. */
+typedef struct {
+  int n_if;
+  int bits;
+  int64_t n_fft;
+  int64_t hop;
+  int window;
+  const float* taps;
+  int n_pair;
+  const int* pairs;
+  int accum_fp64;
+  int device;
+  int max_batch_segments;
+} polaris_config;
+
+/* Stokes parameters for integrate (Eq. 2): feed type, parallactic angle psi_m
+ * (radians, used as written in Eq. 2), and per-pair complex voltage gains
+ * gains[4*p + 0..3] = (Ga re, Ga im, Gb re, Gb im); gains == NULL means G = 1. */
+typedef struct {
+  int feed;
+  double psi_m;
+  const float* gains;
+} polaris_stokes_params;
+
+/* Create a spectrometer.  Allocates all device state (accumulators, twiddle and
+ * window tables, scratch).  Returns POLARIS_EINVAL for invalid config (out is
+ * untouched), POLARIS_ENOMEM / POLARIS_ECUDA on allocation / CUDA failure. */
+int spectrometer_create(const polaris_config* cfg, polaris_spec** out);
+
+/* Feed n_samples_per_if new samples of every IF stream and accumulate all whole
+ * segments they complete into the current integration.
+ *   packed[i]   pointer to IF i's words (n_samples_per_if * bits / 32 words);
+ *               host memory when on_device == 0, device memory otherwise.  Must
+ *               be 4-byte aligned.
+ *   n_samples_per_if  >= 0, a multiple of 32/bits.
+ *   cuda_stream cudaStream_t to order the work on (NULL = legacy default stream).
+ * Host input has been read when the call returns.  Device input is read in
+ * stream order: keep it alive until the stream reaches this point.  Work is
+ * asynchronous with respect to the host for device input. */
+int spectrometer_feed(polaris_spec* s, const void* const* packed, int64_t n_samples_per_if, int on_device,
+                      void* cuda_stream);
+
+/* Close the current integration: form autos, crosses and Stokes from the
+ * accumulated sums, copy them to the HOST buffers given (NULL skips an output),
+ * and reset the accumulators (carried samples persist).  Synchronous.
+ *   autos   [n_if][N/2+1] float
+ *   cross   [n_pair][N/2+1][2] float (re, im) = sum X_a conj(X_b)
+ *   stokes  [n_pair][4][N/2+1] float (I, Q, U, V)
+ *   n_segments_out  segments per IF in this integration (may be NULL)
+ * params == NULL means linear feeds, psi_m = 0, unit gains.
+ * Returns POLARIS_ESTATE when no segment has been accumulated. */
+int spectrometer_integrate(polaris_spec* s, const polaris_stokes_params* params, float* autos, float* cross,
+                           float* stokes, int64_t* n_segments_out);
+
+/* As spectrometer_integrate, but the outputs are DEVICE buffers of the same
+ * layouts, written in stream order on cuda_stream (no host synchronisation). */
+int spectrometer_integrate_device(polaris_spec* s, const polaris_stokes_params* params, float* d_autos, float* d_cross,
+                                  float* d_stokes, int64_t* n_segments_out, void* cuda_stream);
+
+/* Number of output bins (N/2 + 1), IFs and pairs of a handle. */
+int64_t spectrometer_n_bins(const polaris_spec* s);
+int spectrometer_n_pairs(const polaris_spec* s);
+
+/* The data-translation step alone (Fig. 2 caption: integer codes to floats),
+ * for bit-exact checks: decode n samples of one packed stream (host words) into
+ * host floats `out`, on the GPU.  n must be a multiple of 32/bits. */
+int spectrometer_debug_unpack(polaris_spec* s, const void* packed, int64_t n, float* out);
+
+/* Free all resources.  NULL is ignored. */
+void spectrometer_destroy(polaris_spec* s);
+
+/* Text of the last error on this handle ("" if none); for s == NULL, the last
+ * error of a failed spectrometer_create in this thread. */
+const char* spectrometer_last_error(const polaris_spec* s);
+
+/* Test hook: cap the bytes of device memory that later spectrometer_create
+ * calls may allocate (-1 = no cap), so that allocation failure can be tested
+ * without exhausting the GPU. */
+void polaris_set_alloc_limit(int64_t bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POLARIS_H */

@@ -1,0 +1,650 @@
+// C ABI of the PolariS hot path (declared in include/polaris.h) and the two small
+// kernels that sit around the FFT-correlator: the stand-alone data-translation kernel
+// (bit-exact checks) and the readout kernel that turns the integration accumulators
+// into autos, crosses and Stokes I, Q, U, V (Eq. 2).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/polaris.h"
+#include "polaris_kernels.cuh"
+
+namespace polaris {
+// per-size batch runners, one translation unit each (polaris_n<LOGN>.cu)
+#define POLARIS_DECLARE(LOGN) extern template cudaError_t run_batch<LOGN>(const BatchArgs&, cudaStream_t);
+POLARIS_DECLARE(4)
+POLARIS_DECLARE(5)
+POLARIS_DECLARE(6)
+POLARIS_DECLARE(7)
+POLARIS_DECLARE(8)
+POLARIS_DECLARE(9)
+POLARIS_DECLARE(10)
+POLARIS_DECLARE(11)
+POLARIS_DECLARE(12)
+POLARIS_DECLARE(13)
+POLARIS_DECLARE(14)
+POLARIS_DECLARE(15)
+POLARIS_DECLARE(16)
+POLARIS_DECLARE(17)
+POLARIS_DECLARE(18)
+POLARIS_DECLARE(19)
+#undef POLARIS_DECLARE
+
+static cudaError_t dispatch_batch(int logn, const BatchArgs& a, cudaStream_t st) {
+  switch (logn) {
+    case 4: return run_batch<4>(a, st);
+    case 5: return run_batch<5>(a, st);
+    case 6: return run_batch<6>(a, st);
+    case 7: return run_batch<7>(a, st);
+    case 8: return run_batch<8>(a, st);
+    case 9: return run_batch<9>(a, st);
+    case 10: return run_batch<10>(a, st);
+    case 11: return run_batch<11>(a, st);
+    case 12: return run_batch<12>(a, st);
+    case 13: return run_batch<13>(a, st);
+    case 14: return run_batch<14>(a, st);
+    case 15: return run_batch<15>(a, st);
+    case 16: return run_batch<16>(a, st);
+    case 17: return run_batch<17>(a, st);
+    case 18: return run_batch<18>(a, st);
+    case 19: return run_batch<19>(a, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// data translation alone
+// ---------------------------------------------------------------------------------------
+template <int BITS>
+__global__ void k_unpack(const uint32_t* __restrict__ w, long long n, float* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned long long bit = (unsigned long long)i * BITS;
+  out[i] = decode_level<BITS>(w[bit >> 5], (uint32_t)(bit & 31u));
+}
+
+// ---------------------------------------------------------------------------------------
+// readout + Stokes (Eq. 2).  One thread per output bin k and FFT pair f.
+// Native accumulator order of FFT pair f (k = c + N1 d):
+//   c = 0         : slot d              (d = 0 .. N2/2)
+//   c = N1/2      : slot N2/2 + 1 + d   (d = 0 .. N2/2 - 2), d = N2/2 - 1 in slot UPS*N2
+//   0 < c < N1/2  : slot c N2 + d       (d < N2/2)
+//   c > N1/2      : slot (N1 - c) N2 + (N2 - 1 - d), cross conjugated
+// Each slot holds sum |S|^2, |D|^2 and Re, Im of i S conj(D) with S = 2X, D = 2iY.
+// ---------------------------------------------------------------------------------------
+struct ReadoutArgs {
+  const void* acc;
+  int fp64;
+  int N1, N2, UPS, nbin, native;
+  int fa[kMaxIF], fb[kMaxIF], fcorr[kMaxIF];
+  float* autos;
+  float* cross;
+  float* stokes;
+  int feed;
+  float c2, s2;
+  float inv_ga2[kMaxIF], inv_gb2[kMaxIF], ig_re[kMaxIF], ig_im[kMaxIF];  // 1/|Ga|^2, 1/|Gb|^2, 1/(Ga conj Gb)
+};
+
+__global__ void k_readout(ReadoutArgs a) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x, f = blockIdx.y;
+  if (k >= a.nbin) return;
+  const int c = k & (a.N1 - 1), d = k / a.N1;
+  int idx;
+  bool cj = false;
+  if (c == 0) idx = d;
+  else if (c == a.N1 / 2) idx = (d <= a.N2 / 2 - 2) ? a.N2 / 2 + 1 + d : a.UPS * a.N2;
+  else if (c < a.N1 / 2) idx = c * a.N2 + d;
+  else {
+    idx = (a.N1 - c) * a.N2 + (a.N2 - 1 - d);
+    cj = true;
+  }
+  const size_t off = (size_t)f * a.native + idx;
+  float xx, yy, xr, xi;
+  if (a.fp64) {
+    const double* p = reinterpret_cast<const double*>(a.acc) + 4 * off;
+    xx = (float)(0.25 * p[0]);
+    yy = (float)(0.25 * p[1]);
+    xr = (float)(0.25 * p[2]);
+    xi = (float)(0.25 * p[3]);
+  } else {
+    const float4 v = reinterpret_cast<const float4*>(a.acc)[off];
+    xx = 0.25f * v.x;
+    yy = 0.25f * v.y;
+    xr = 0.25f * v.z;
+    xi = 0.25f * v.w;
+  }
+  if (cj) xi = -xi;
+  if (a.autos) {
+    a.autos[(size_t)a.fa[f] * a.nbin + k] = xx;
+    if (a.fb[f] >= 0) a.autos[(size_t)a.fb[f] * a.nbin + k] = yy;
+  }
+  const int p = a.fcorr[f];
+  if (p < 0) return;
+  if (a.cross) {
+    a.cross[((size_t)p * a.nbin + k) * 2 + 0] = xr;
+    a.cross[((size_t)p * a.nbin + k) * 2 + 1] = xi;
+  }
+  if (a.stokes) {
+    const float x = xx * a.inv_ga2[p], y = yy * a.inv_gb2[p];
+    const float cr = xr * a.ig_re[p] - xi * a.ig_im[p];
+    const float ci = xr * a.ig_im[p] + xi * a.ig_re[p];
+    float I, Q, Uq, V;
+    if (a.feed == POLARIS_FEED_LINEAR) {
+      I = 0.5f * (x + y);
+      Q = 0.5f * (a.c2 * (x - y) - a.s2 * 2.0f * cr);
+      Uq = 0.5f * (a.s2 * (x - y) + a.c2 * 2.0f * cr);
+      V = ci;
+    } else {
+      I = 0.5f * (x + y);
+      V = 0.5f * (x - y);
+      Q = a.c2 * cr - a.s2 * ci;
+      Uq = a.s2 * cr + a.c2 * ci;
+    }
+    float* o = a.stokes + (size_t)p * 4 * a.nbin + k;
+    o[0] = I;
+    o[a.nbin] = Q;
+    o[2 * (size_t)a.nbin] = Uq;
+    o[3 * (size_t)a.nbin] = V;
+  }
+}
+
+static int host_plan_n2(int logn) { return 1 << plan_log_n2(logn); }
+
+}  // namespace polaris
+
+using namespace polaris;
+
+// ---------------------------------------------------------------------------------------
+// handle
+// ---------------------------------------------------------------------------------------
+struct polaris_spec {
+  int n_if = 0, bits = 0, window = 0, accum_fp64 = 0, device = 0, num_sms = 0;
+  int logn = 0;
+  int64_t N = 0, hop = 0, nbin = 0, spw = 0;
+  int N1 = 0, N2 = 0, UPS = 0, native = 0;
+  int n_pair = 0, n_fpair = 0;
+  int fa[kMaxIF], fb[kMaxIF], fcorr[kMaxIF];
+  int max_batch = 0;
+  float* d_taps = nullptr;
+  float2* d_tw = nullptr;
+  void* d_acc = nullptr;
+  float2* d_scratch = nullptr;
+  uint32_t* d_carry[2] = {nullptr, nullptr};  // ping-pong, each n_if * carry_words_cap
+  int carry_sel = 0;
+  int64_t carry_len = 0;                      // carried samples per IF
+  uint32_t* d_stage = nullptr;                // n_if * stage_words_cap
+  uint32_t* d_in = nullptr;                   // n_if * in_words_cap (host-fed input)
+  int64_t in_words_cap = 0;
+  int64_t carry_words_cap = 0, stage_words_cap = 0;
+  float* d_out_autos = nullptr;
+  float* d_out_cross = nullptr;
+  float* d_out_stokes = nullptr;
+  cudaEvent_t ev_h2d = nullptr;
+  int64_t seg_acc = 0;  // segments accumulated in the open integration
+  bool broken = false;
+  std::string err;
+};
+
+static thread_local std::string g_create_err;
+static int64_t g_alloc_limit = -1;
+
+static int set_err(polaris_spec* s, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (s) {
+    s->err = buf;
+    if (code == POLARIS_ECUDA) s->broken = true;
+  } else {
+    g_create_err = buf;
+  }
+  return code;
+}
+
+#define CUDA_OR_FAIL(s, call)                                                                        \
+  do {                                                                                               \
+    cudaError_t e_ = (call);                                                                         \
+    if (e_ != cudaSuccess) return set_err((s), POLARIS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+static void free_all(polaris_spec* s) {
+  cudaFree(s->d_taps);
+  cudaFree(s->d_tw);
+  cudaFree(s->d_acc);
+  cudaFree(s->d_scratch);
+  cudaFree(s->d_carry[0]);
+  cudaFree(s->d_carry[1]);
+  cudaFree(s->d_stage);
+  cudaFree(s->d_in);
+  cudaFree(s->d_out_autos);
+  cudaFree(s->d_out_cross);
+  cudaFree(s->d_out_stokes);
+  if (s->ev_h2d) cudaEventDestroy(s->ev_h2d);
+}
+
+extern "C" void polaris_set_alloc_limit(int64_t bytes) { g_alloc_limit = bytes; }
+
+extern "C" int spectrometer_create(const polaris_config* cfg, polaris_spec** out) {
+  if (!cfg || !out) return set_err(nullptr, POLARIS_EINVAL, "null config or output pointer");
+  const polaris_config& c = *cfg;
+  if (c.n_if < 1 || c.n_if > kMaxIF) return set_err(nullptr, POLARIS_EINVAL, "n_if must be in [1, %d]", kMaxIF);
+  if (!(c.bits == 1 || c.bits == 2 || c.bits == 4 || c.bits == 8))
+    return set_err(nullptr, POLARIS_EINVAL, "bits must be 1, 2, 4 or 8");
+  const int64_t N = c.n_fft;
+  if (N < 16 || N > (1 << 19) || (N & (N - 1)))
+    return set_err(nullptr, POLARIS_EINVAL, "n_fft must be a power of two in [16, 524288]");
+  const int64_t spw = 32 / c.bits;
+  if (N < spw) return set_err(nullptr, POLARIS_EINVAL, "n_fft must be at least 32/bits samples");
+  const int64_t hop = c.hop == 0 ? N : c.hop;
+  if (hop < 1 || hop > N || hop % spw)
+    return set_err(nullptr, POLARIS_EINVAL, "hop must be in (0, n_fft] and a multiple of 32/bits");
+  if (c.window < POLARIS_WIN_RECT || c.window > POLARIS_WIN_CUSTOM)
+    return set_err(nullptr, POLARIS_EINVAL, "unknown window kind");
+  if (c.window == POLARIS_WIN_CUSTOM && !c.taps) return set_err(nullptr, POLARIS_EINVAL, "custom window needs taps");
+  if (c.max_batch_segments < 0) return set_err(nullptr, POLARIS_EINVAL, "max_batch_segments must be >= 0");
+  // correlation pairs
+  int pairs[2 * kMaxIF];
+  int n_pair = 0;
+  if (c.pairs) {
+    if (c.n_pair < 0 || 2 * c.n_pair > c.n_if) return set_err(nullptr, POLARIS_EINVAL, "bad n_pair");
+    n_pair = c.n_pair;
+    for (int i = 0; i < 2 * n_pair; ++i) pairs[i] = c.pairs[i];
+  } else {
+    if (c.n_pair != 0) return set_err(nullptr, POLARIS_EINVAL, "n_pair given without pairs");
+    if (c.n_if % 2 == 0) {
+      n_pair = c.n_if / 2;
+      for (int i = 0; i < n_pair; ++i) {
+        pairs[2 * i] = i;
+        pairs[2 * i + 1] = i + n_pair;
+      }
+    }
+  }
+  int used[kMaxIF] = {0};
+  for (int i = 0; i < 2 * n_pair; ++i) {
+    if (pairs[i] < 0 || pairs[i] >= c.n_if) return set_err(nullptr, POLARIS_EINVAL, "pair index out of range");
+    if (used[pairs[i]]++) return set_err(nullptr, POLARIS_EINVAL, "an IF appears in more than one pair");
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= 0) {
+    cudaGetLastError();
+    return set_err(nullptr, POLARIS_ECUDA, "no CUDA device available");
+  }
+  if (c.device < 0 || c.device >= ndev) return set_err(nullptr, POLARIS_EINVAL, "device ordinal out of range");
+
+  polaris_spec* s = new polaris_spec();
+  s->n_if = c.n_if;
+  s->bits = c.bits;
+  s->window = c.window;
+  s->accum_fp64 = c.accum_fp64 ? 1 : 0;
+  s->device = c.device;
+  s->N = N;
+  s->hop = hop;
+  s->spw = spw;
+  s->nbin = N / 2 + 1;
+  int logn = 0;
+  while ((1LL << logn) < N) ++logn;
+  s->logn = logn;
+  s->N2 = host_plan_n2(logn);
+  s->N1 = (int)(N / s->N2);
+  s->UPS = s->N1 / 2;
+  s->native = s->UPS * s->N2 + 1;
+  s->n_pair = n_pair;
+  // FFT pairs: correlation pairs first, then the remaining IFs two at a time
+  int nf = 0;
+  for (int p = 0; p < n_pair; ++p) {
+    s->fa[nf] = pairs[2 * p];
+    s->fb[nf] = pairs[2 * p + 1];
+    s->fcorr[nf] = p;
+    ++nf;
+  }
+  int pending = -1;
+  for (int i = 0; i < c.n_if; ++i) {
+    if (used[i]) continue;
+    if (pending < 0) pending = i;
+    else {
+      s->fa[nf] = pending;
+      s->fb[nf] = i;
+      s->fcorr[nf] = -1;
+      ++nf;
+      pending = -1;
+    }
+  }
+  if (pending >= 0) {
+    s->fa[nf] = pending;
+    s->fb[nf] = -1;
+    s->fcorr[nf] = -1;
+    ++nf;
+  }
+  s->n_fpair = nf;
+  for (int f = nf; f < kMaxIF; ++f) s->fa[f] = s->fb[f] = s->fcorr[f] = -1;
+
+  DeviceGuard dg(c.device);
+  cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, c.device);
+  // batch size: keep the per-batch scratch (segments * FFT pairs * N * 8 bytes) near 48 MB
+  if (c.max_batch_segments > 0) s->max_batch = c.max_batch_segments;
+  else {
+    const int64_t per_seg = (int64_t)nf * N * 8;
+    int64_t mb = (48LL << 20) / per_seg;
+    s->max_batch = (int)(mb < 1 ? 1 : (mb > 4096 ? 4096 : mb));
+  }
+  s->carry_words_cap = N / spw;               // carried samples < N
+  s->stage_words_cap = 2 * N / spw;           // staging < carry + N samples
+  const size_t acc_bytes = (size_t)nf * s->native * 4 * (s->accum_fp64 ? 8 : 4);
+  const size_t bytes_tw = (size_t)s->N2 * (s->UPS + 1) * sizeof(float2);
+  const size_t bytes_scratch = (size_t)s->max_batch * nf * N * sizeof(float2);
+  const size_t bytes_carry = (size_t)c.n_if * s->carry_words_cap * 4;
+  const size_t bytes_stage = (size_t)c.n_if * s->stage_words_cap * 4;
+  const size_t bytes_out = (size_t)s->nbin * 4 * (c.n_if + 2 * n_pair + 4 * n_pair);
+  const size_t total = acc_bytes + bytes_tw + bytes_scratch + 2 * bytes_carry + bytes_stage + bytes_out +
+                       (c.window != POLARIS_WIN_RECT ? N * 4 : 0);
+  if (g_alloc_limit >= 0 && (int64_t)total > g_alloc_limit) {
+    delete s;
+    return set_err(nullptr, POLARIS_ENOMEM, "device allocation of %zu bytes exceeds the limit %lld", total,
+                   (long long)g_alloc_limit);
+  }
+  auto alloc = [&](void** p, size_t bytes) -> bool {
+    if (bytes == 0) bytes = 16;
+    return cudaMalloc(p, bytes) == cudaSuccess;
+  };
+  bool ok = alloc((void**)&s->d_acc, acc_bytes) && alloc((void**)&s->d_tw, bytes_tw) &&
+            alloc((void**)&s->d_scratch, bytes_scratch) && alloc((void**)&s->d_carry[0], bytes_carry) &&
+            alloc((void**)&s->d_carry[1], bytes_carry) && alloc((void**)&s->d_stage, bytes_stage) &&
+            alloc((void**)&s->d_out_autos, (size_t)s->nbin * 4 * c.n_if) &&
+            alloc((void**)&s->d_out_cross, (size_t)s->nbin * 8 * (n_pair ? n_pair : 1)) &&
+            alloc((void**)&s->d_out_stokes, (size_t)s->nbin * 16 * (n_pair ? n_pair : 1));
+  if (ok && c.window != POLARIS_WIN_RECT) ok = alloc((void**)&s->d_taps, N * 4);
+  if (!ok) {
+    cudaGetLastError();
+    free_all(s);
+    delete s;
+    return set_err(nullptr, POLARIS_ENOMEM, "cudaMalloc failed");
+  }
+  // twiddles W_N^{b u} for b < N2, u <= N1/2, in FP64 then rounded
+  std::vector<float2> tw((size_t)s->N2 * (s->UPS + 1));
+  for (int b = 0; b < s->N2; ++b)
+    for (int u = 0; u <= s->UPS; ++u) {
+      const int64_t e = ((int64_t)b * u) % N;
+      const double ang = -2.0 * M_PI * (double)e / (double)N;
+      tw[(size_t)b * (s->UPS + 1) + u] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+    }
+  cudaError_t e = cudaMemcpy(s->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && c.window != POLARIS_WIN_RECT) {
+    std::vector<float> taps(N);
+    for (int64_t n = 0; n < N; ++n)
+      taps[n] = c.window == POLARIS_WIN_HANN ? (float)(0.5 - 0.5 * std::cos(2.0 * M_PI * (double)n / (double)N))
+                                             : c.taps[n];
+    e = cudaMemcpy(s->d_taps, taps.data(), N * 4, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaMemset(s->d_acc, 0, acc_bytes);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_h2d, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_all(s);
+    delete s;
+    return set_err(nullptr, POLARIS_ECUDA, "create: %s", cudaGetErrorString(e));
+  }
+  *out = s;
+  return POLARIS_OK;
+}
+
+extern "C" void spectrometer_destroy(polaris_spec* s) {
+  if (!s) return;
+  {
+    DeviceGuard dg(s->device);
+    cudaDeviceSynchronize();
+    free_all(s);
+  }
+  delete s;
+}
+
+extern "C" const char* spectrometer_last_error(const polaris_spec* s) {
+  return s ? s->err.c_str() : g_create_err.c_str();
+}
+
+extern "C" int64_t spectrometer_n_bins(const polaris_spec* s) { return s ? s->nbin : -1; }
+extern "C" int spectrometer_n_pairs(const polaris_spec* s) { return s ? s->n_pair : -1; }
+
+static int check_usable(polaris_spec* s) {
+  if (!s) return POLARIS_EINVAL;
+  if (s->broken) return set_err(s, POLARIS_ESTATE, "handle unusable after an earlier CUDA error: %s", s->err.c_str());
+  return POLARIS_OK;
+}
+
+extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int64_t n, int on_device,
+                                 void* cuda_stream) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (!packed) return set_err(s, POLARIS_EINVAL, "packed is NULL");
+  if (n < 0 || n % s->spw) return set_err(s, POLARIS_EINVAL, "n_samples_per_if must be >= 0 and a multiple of %lld",
+                                          (long long)s->spw);
+  for (int i = 0; i < s->n_if; ++i) {
+    if (!packed[i]) return set_err(s, POLARIS_EINVAL, "packed[%d] is NULL", i);
+    if (reinterpret_cast<uintptr_t>(packed[i]) & 3) return set_err(s, POLARIS_EINVAL, "packed[%d] is not 4-byte aligned", i);
+  }
+  if (n == 0) return POLARIS_OK;
+  DeviceGuard dg(s->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  const int64_t nw = n / s->spw;
+  const uint32_t* src[kMaxIF] = {nullptr};
+  if (!on_device) {
+    if (nw > s->in_words_cap) {
+      CUDA_OR_FAIL(s, cudaStreamSynchronize(st));
+      cudaFree(s->d_in);
+      s->d_in = nullptr;
+      s->in_words_cap = 0;
+      if (cudaMalloc((void**)&s->d_in, (size_t)nw * 4 * s->n_if) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(s, POLARIS_ENOMEM, "cannot allocate %lld bytes of device input staging",
+                       (long long)(nw * 4 * s->n_if));
+      }
+      s->in_words_cap = nw;
+    }
+    for (int i = 0; i < s->n_if; ++i) {
+      CUDA_OR_FAIL(s, cudaMemcpyAsync(s->d_in + (size_t)i * s->in_words_cap, packed[i], (size_t)nw * 4,
+                                      cudaMemcpyHostToDevice, st));
+      src[i] = s->d_in + (size_t)i * s->in_words_cap;
+    }
+    CUDA_OR_FAIL(s, cudaEventRecord(s->ev_h2d, st));
+  } else {
+    for (int i = 0; i < s->n_if; ++i) src[i] = static_cast<const uint32_t*>(packed[i]);
+  }
+  const int64_t N = s->N, hop = s->hop, spw = s->spw;
+  const int64_t carry = s->carry_len;
+  const int64_t total = carry + n;
+  const int64_t nseg = total >= N ? (total - N) / hop + 1 : 0;
+  const int64_t n0 = nseg < (carry + hop - 1) / hop ? nseg : (carry + hop - 1) / hop;
+  uint32_t* cur_carry = s->d_carry[s->carry_sel];
+  if (n0 > 0) {
+    const int64_t stage_len = (n0 - 1) * hop + N;  // samples: carry + (stage_len - carry) new ones
+    for (int i = 0; i < s->n_if; ++i) {
+      uint32_t* dst = s->d_stage + (size_t)i * s->stage_words_cap;
+      if (carry)
+        CUDA_OR_FAIL(s, cudaMemcpyAsync(dst, cur_carry + (size_t)i * s->carry_words_cap, (size_t)(carry / spw) * 4,
+                                        cudaMemcpyDeviceToDevice, st));
+      CUDA_OR_FAIL(s, cudaMemcpyAsync(dst + carry / spw, src[i], (size_t)((stage_len - carry) / spw) * 4,
+                                      cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  BatchArgs a;
+  memset(&a, 0, sizeof a);
+  for (int i = 0; i < s->n_if; ++i) {
+    a.in.src0[i] = s->d_stage + (size_t)i * s->stage_words_cap;
+    a.in.src1[i] = src[i] + (n0 * hop - carry) / spw;
+  }
+  a.in.hop_w = hop / spw;
+  a.in.n0 = (int)n0;
+  for (int f = 0; f < kMaxIF; ++f) {
+    a.fa[f] = s->fa[f];
+    a.fb[f] = s->fb[f];
+  }
+  a.n_fpair = s->n_fpair;
+  a.taps = s->d_taps;
+  a.scratch = s->d_scratch;
+  a.tw = s->d_tw;
+  a.acc = s->d_acc;
+  a.fp64 = s->accum_fp64;
+  a.bits = s->bits;
+  a.num_sms = s->num_sms;
+  for (int64_t s0 = 0; s0 < nseg; s0 += s->max_batch) {
+    a.seg0 = (int)s0;
+    a.nseg = (int)(nseg - s0 < s->max_batch ? nseg - s0 : s->max_batch);
+    cudaError_t e = dispatch_batch(s->logn, a, st);
+    if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "FFT-correlator launch: %s", cudaGetErrorString(e));
+  }
+  // carry the samples after the last whole segment: stream positions [nseg*hop, total)
+  const int64_t keep0 = nseg * hop, keep = total - keep0;
+  uint32_t* nxt = s->d_carry[s->carry_sel ^ 1];
+  for (int i = 0; i < s->n_if && keep > 0; ++i) {
+    uint32_t* dst = nxt + (size_t)i * s->carry_words_cap;
+    if (keep0 >= carry) {
+      CUDA_OR_FAIL(s, cudaMemcpyAsync(dst, src[i] + (keep0 - carry) / spw, (size_t)(keep / spw) * 4,
+                                      cudaMemcpyDeviceToDevice, st));
+    } else {
+      const int64_t from_old = carry - keep0;
+      CUDA_OR_FAIL(s, cudaMemcpyAsync(dst, cur_carry + (size_t)i * s->carry_words_cap + keep0 / spw,
+                                      (size_t)(from_old / spw) * 4, cudaMemcpyDeviceToDevice, st));
+      CUDA_OR_FAIL(s, cudaMemcpyAsync(dst + from_old / spw, src[i], (size_t)(n / spw) * 4, cudaMemcpyDeviceToDevice, st));
+    }
+  }
+  s->carry_sel ^= 1;
+  s->carry_len = keep;
+  s->seg_acc += nseg;
+  if (!on_device) CUDA_OR_FAIL(s, cudaEventSynchronize(s->ev_h2d));  // host input has been read
+  return POLARIS_OK;
+}
+
+static int fill_readout(polaris_spec* s, const polaris_stokes_params* prm, ReadoutArgs& r) {
+  memset(&r, 0, sizeof r);
+  r.acc = s->d_acc;
+  r.fp64 = s->accum_fp64;
+  r.N1 = s->N1;
+  r.N2 = s->N2;
+  r.UPS = s->UPS;
+  r.nbin = (int)s->nbin;
+  r.native = s->native;
+  for (int f = 0; f < kMaxIF; ++f) {
+    r.fa[f] = s->fa[f];
+    r.fb[f] = s->fb[f];
+    r.fcorr[f] = s->fcorr[f];
+  }
+  const int feed = prm ? prm->feed : POLARIS_FEED_LINEAR;
+  if (feed != POLARIS_FEED_LINEAR && feed != POLARIS_FEED_CIRCULAR) return set_err(s, POLARIS_EINVAL, "unknown feed type");
+  const double psi = prm ? prm->psi_m : 0.0;
+  r.feed = feed;
+  r.c2 = (float)std::cos(2.0 * psi);
+  r.s2 = (float)std::sin(2.0 * psi);
+  for (int p = 0; p < s->n_pair; ++p) {
+    double gar = 1, gai = 0, gbr = 1, gbi = 0;
+    if (prm && prm->gains) {
+      gar = prm->gains[4 * p + 0];
+      gai = prm->gains[4 * p + 1];
+      gbr = prm->gains[4 * p + 2];
+      gbi = prm->gains[4 * p + 3];
+    }
+    const double gaa = gar * gar + gai * gai, gbb = gbr * gbr + gbi * gbi;
+    if (gaa == 0.0 || gbb == 0.0) return set_err(s, POLARIS_EINVAL, "zero gain for pair %d", p);
+    // g = Ga conj(Gb); 1/g = conj(g)/|g|^2
+    const double gr = gar * gbr + gai * gbi, gi = gai * gbr - gar * gbi, g2 = gr * gr + gi * gi;
+    r.inv_ga2[p] = (float)(1.0 / gaa);
+    r.inv_gb2[p] = (float)(1.0 / gbb);
+    r.ig_re[p] = (float)(gr / g2);
+    r.ig_im[p] = (float)(-gi / g2);
+  }
+  return POLARIS_OK;
+}
+
+extern "C" int spectrometer_integrate_device(polaris_spec* s, const polaris_stokes_params* prm, float* d_autos,
+                                             float* d_cross, float* d_stokes, int64_t* n_segments_out,
+                                             void* cuda_stream) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (s->seg_acc == 0) return set_err(s, POLARIS_ESTATE, "no segment accumulated since the last integrate");
+  ReadoutArgs r;
+  rc = fill_readout(s, prm, r);
+  if (rc) return rc;
+  DeviceGuard dg(s->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  r.autos = d_autos;
+  r.cross = d_cross;
+  r.stokes = d_stokes;
+  dim3 grid((unsigned)((s->nbin + 255) / 256), (unsigned)s->n_fpair);
+  k_readout<<<grid, 256, 0, st>>>(r);
+  CUDA_OR_FAIL(s, cudaGetLastError());
+  const size_t acc_bytes = (size_t)s->n_fpair * s->native * 4 * (s->accum_fp64 ? 8 : 4);
+  CUDA_OR_FAIL(s, cudaMemsetAsync(s->d_acc, 0, acc_bytes, st));
+  if (n_segments_out) *n_segments_out = s->seg_acc;
+  s->seg_acc = 0;
+  return POLARIS_OK;
+}
+
+extern "C" int spectrometer_integrate(polaris_spec* s, const polaris_stokes_params* prm, float* autos, float* cross,
+                                      float* stokes, int64_t* n_segments_out) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (s->seg_acc == 0) return set_err(s, POLARIS_ESTATE, "no segment accumulated since the last integrate");
+  DeviceGuard dg(s->device);
+  rc = spectrometer_integrate_device(s, prm, s->d_out_autos, s->n_pair ? s->d_out_cross : nullptr,
+                                     s->n_pair ? s->d_out_stokes : nullptr, n_segments_out, nullptr);
+  if (rc) return rc;
+  if (autos)
+    CUDA_OR_FAIL(s, cudaMemcpy(autos, s->d_out_autos, (size_t)s->nbin * 4 * s->n_if, cudaMemcpyDeviceToHost));
+  if (cross && s->n_pair)
+    CUDA_OR_FAIL(s, cudaMemcpy(cross, s->d_out_cross, (size_t)s->nbin * 8 * s->n_pair, cudaMemcpyDeviceToHost));
+  if (stokes && s->n_pair)
+    CUDA_OR_FAIL(s, cudaMemcpy(stokes, s->d_out_stokes, (size_t)s->nbin * 16 * s->n_pair, cudaMemcpyDeviceToHost));
+  CUDA_OR_FAIL(s, cudaDeviceSynchronize());
+  return POLARIS_OK;
+}
+
+extern "C" int spectrometer_debug_unpack(polaris_spec* s, const void* packed, int64_t n, float* out) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (!packed || !out) return set_err(s, POLARIS_EINVAL, "null pointer");
+  if (n < 0 || n % s->spw) return set_err(s, POLARIS_EINVAL, "n must be >= 0 and a multiple of %lld", (long long)s->spw);
+  if (n == 0) return POLARIS_OK;
+  DeviceGuard dg(s->device);
+  uint32_t* dw = nullptr;
+  float* df = nullptr;
+  const size_t nw = (size_t)(n / s->spw);
+  if (cudaMalloc((void**)&dw, nw * 4) != cudaSuccess || cudaMalloc((void**)&df, (size_t)n * 4) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(dw);
+    cudaFree(df);
+    return set_err(s, POLARIS_ENOMEM, "debug_unpack allocation failed");
+  }
+  cudaError_t e = cudaMemcpy(dw, packed, nw * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    switch (s->bits) {
+      case 1: k_unpack<1><<<grid, 256>>>(dw, n, df); break;
+      case 2: k_unpack<2><<<grid, 256>>>(dw, n, df); break;
+      case 4: k_unpack<4><<<grid, 256>>>(dw, n, df); break;
+      default: k_unpack<8><<<grid, 256>>>(dw, n, df); break;
+    }
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, df, (size_t)n * 4, cudaMemcpyDeviceToHost);
+  cudaFree(dw);
+  cudaFree(df);
+  if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "debug_unpack: %s", cudaGetErrorString(e));
+  return POLARIS_OK;
+}

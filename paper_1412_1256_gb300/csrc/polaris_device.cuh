@@ -1,0 +1,215 @@
+// Device building blocks of the PolariS hot path for sm_103a:
+//   * compile-time twiddles (own octant-reduced Taylor series, FP64, rounded once to f32)
+//   * in-register radix-2 DIT transforms with the twiddle folded into the butterfly
+//     FMAs (cosine-factored form: a +- W b = a +- wr (b + (wi/wr) i b), 6 FMAs)
+//   * the data-translation step (b-bit code -> float level, exact, no I2F)
+//   * the per-size two-phase plan N = N1 * N2.
+//
+// The transform is the segment FFT of the paper (Fig. 2 caption: "FFT"), unnormalised,
+// forward sign e^{-i}.  Two real IF streams x, y of a pair are transformed together as
+// z = x + i y (one complex FFT of N points per pair-segment).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <type_traits>
+
+namespace polaris {
+
+// ----------------------------------------------------------------------------------------
+// compile-time trigonometry
+// ----------------------------------------------------------------------------------------
+namespace ct {
+constexpr double kPi = 3.141592653589793238462643383279502884;
+constexpr double sin_small(double x) {  // |x| <= pi/4; Taylor series, error << 1e-17
+  double x2 = x * x, t = x, s = x;
+  for (int n = 1; n <= 13; ++n) {
+    t *= -x2 / (double)((2 * n) * (2 * n + 1));
+    s += t;
+  }
+  return s;
+}
+constexpr double cos_small(double x) {
+  double x2 = x * x, t = 1.0, s = 1.0;
+  for (int n = 1; n <= 13; ++n) {
+    t *= -x2 / (double)((2 * n - 1) * (2 * n));
+    s += t;
+  }
+  return s;
+}
+struct CS {
+  double c, s;
+};
+// (cos, sin) of 2 pi k / L with exact integer octant reduction.
+constexpr CS cossin2pi(long k, long L) {
+  k %= L;
+  if (k < 0) k += L;
+  const long e = 8 * k;       // angle = (pi/4) * e / L
+  const long o = e / L;       // octant 0..7
+  const long r = e - o * L;   // remainder in [0, L)
+  const long q = o / 2;       // quadrant
+  const long num = (o % 2) * L + r;  // angle inside the quadrant = (pi/4) num / L, num in [0, 2L)
+  double ca = 0, sa = 0;
+  if (num <= L) {
+    const double a = (kPi / 4.0) * ((double)num / (double)L);
+    ca = cos_small(a);
+    sa = sin_small(a);
+  } else {
+    const double b = (kPi / 4.0) * ((double)(2 * L - num) / (double)L);
+    ca = sin_small(b);
+    sa = cos_small(b);
+  }
+  if (q == 0) return CS{ca, sa};
+  if (q == 1) return CS{-sa, ca};
+  if (q == 2) return CS{-ca, -sa};
+  return CS{sa, -ca};
+}
+constexpr double dabs(double v) { return v < 0 ? -v : v; }
+constexpr int ilog2(int v) { return v <= 1 ? 0 : 1 + ilog2(v / 2); }
+constexpr int bitrev(int i, int L) {
+  int r = 0;
+  for (int b = 1; b < L; b <<= 1) {
+    r = (r << 1) | (i & 1);
+    i >>= 1;
+  }
+  return r;
+}
+}  // namespace ct
+
+// static for over [B, E): f(integral_constant<int, i>)
+template <int B, int E, typename F>
+__device__ __forceinline__ void sfor(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    sfor<B + 1, E>(static_cast<F&&>(f));
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// complex helpers
+// ----------------------------------------------------------------------------------------
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // conj(a) * b
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+
+// Radix-2 DIT butterfly a' = a + W b, b' = a - W b with W = e^{-2 pi i J / SPAN}
+// (compile-time).  W = 1 and W = -i cost 4 adds; other W use the cosine-factored form
+// a +- w (b x-part - t b y-part, ...) with |t| <= 1: 6 FMAs.
+template <int J, int SPAN>
+__device__ __forceinline__ void dit_bfly(float2& a, float2& b) {
+  if constexpr (J == 0) {
+    const float tx = b.x, ty = b.y;
+    b.x = a.x - tx;
+    b.y = a.y - ty;
+    a.x += tx;
+    a.y += ty;
+  } else if constexpr (4 * J == SPAN) {  // W = -i: W b = (b.y, -b.x)
+    const float tx = b.y, ty = -b.x;
+    b.x = a.x - tx;
+    b.y = a.y - ty;
+    a.x += tx;
+    a.y += ty;
+  } else {
+    constexpr ct::CS cs = ct::cossin2pi(J, SPAN);
+    constexpr double wr = cs.c, wi = -cs.s;  // W = wr + i wi
+    if constexpr (ct::dabs(wr) >= ct::dabs(wi)) {
+      constexpr float r = (float)(wi / wr), sc = (float)wr;
+      // W b = wr * ((b.x - r b.y) + i (b.y + r b.x))
+      const float ux = fmaf(-r, b.y, b.x), uy = fmaf(r, b.x, b.y);
+      b.x = fmaf(-sc, ux, a.x);
+      b.y = fmaf(-sc, uy, a.y);
+      a.x = fmaf(sc, ux, a.x);
+      a.y = fmaf(sc, uy, a.y);
+    } else {
+      constexpr float r = (float)(wr / wi), sc = (float)wi;
+      // W b = wi * ((r b.x - b.y) + i (r b.y + b.x))
+      const float ux = fmaf(r, b.x, -b.y), uy = fmaf(r, b.y, b.x);
+      b.x = fmaf(-sc, ux, a.x);
+      b.y = fmaf(-sc, uy, a.y);
+      a.x = fmaf(sc, ux, a.x);
+      a.y = fmaf(sc, uy, a.y);
+    }
+  }
+}
+
+// In-register DFT of L points stored at x[OFF + STRIDE * i], i in [0, L):
+// input in bit-reversed order, output in natural order.  X_k = sum_n x_n e^{-2 pi i nk/L}.
+template <int L, int OFF = 0, int STRIDE = 1, typename A>
+__device__ __forceinline__ void dit(A& x) {
+  if constexpr (L > 1) {
+    constexpr int LOG = ct::ilog2(L);
+    sfor<1, LOG + 1>([&](auto s_) {
+      constexpr int span = 1 << decltype(s_)::value;
+      constexpr int half = span / 2;
+      sfor<0, L / span>([&](auto g_) {
+        constexpr int g = decltype(g_)::value * span;
+        sfor<0, half>([&](auto j_) {
+          constexpr int j = decltype(j_)::value;
+          dit_bfly<j, span>(x[OFF + STRIDE * (g + j)], x[OFF + STRIDE * (g + j + half)]);
+        });
+      });
+    });
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// data translation (Fig. 2 caption): b-bit code -> level, exactly, without I2F
+//   b < 8 : level = 2c - (2^b - 1);   b = 8 : two's complement int8
+// Built as a float whose mantissa holds the code: 2^23 + v is exact for 0 <= v < 2^23.
+// ----------------------------------------------------------------------------------------
+template <int BITS>
+__device__ __forceinline__ float decode_level(uint32_t word, uint32_t shift) {
+  const uint32_t c = (word >> shift) & ((1u << BITS) - 1u);
+  if constexpr (BITS == 8) {
+    // (c ^ 0x80) - 128 == int8(c)
+    return __uint_as_float(0x4B000000u | (c ^ 0x80u)) - 8388736.0f;
+  } else {
+    // 2c - (2^b - 1) = (2^23 + 2c) - (2^23 + 2^b - 1)
+    return __uint_as_float(0x4B000000u | (c << 1)) - (8388608.0f + (float)((1 << BITS) - 1));
+  }
+}
+
+// ----------------------------------------------------------------------------------------
+// two-phase plan: N = N1 * N2, n = N2 a + b (a row, b column), k = c + N1 d
+//   phase 1: for each column b, DFT-N1 over a (P points per thread, Q1 = N1/P threads)
+//   phase 2: for each output column c (pairs c, N1 - c), twiddle W_N^{b c}, DFT-N2 over b
+//            (P points per thread, Q2 = N2/P threads), then correlate + accumulate.
+// ----------------------------------------------------------------------------------------
+// (P, N2) per size; N1 = N / N2.  P = points per thread, 2 <= 2 Q2 <= P, Q1 <= P.
+constexpr int plan_p(int logn) { return logn >= 10 ? 32 : (logn >= 8 ? 16 : (logn >= 6 ? 8 : 4)); }
+constexpr int plan_log_n2(int logn) {
+  // 4:2 5:3 6:3 7:4 8:4 9:5 10:5 11:6 12:6 13:7 14:7 15:8 16:8 17:9 18:9 19:9
+  return logn >= 17 ? 9 : (logn + 1) / 2;
+}
+template <int LOGN>
+struct Plan {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int P = plan_p(LOGN);
+  static constexpr int N2 = 1 << plan_log_n2(LOGN);
+  static constexpr int N1 = N / N2;
+  static constexpr int Q1 = N1 / P;
+  static constexpr int Q2 = N2 / P;
+  static constexpr int T1 = 512;  // phase-1 threads
+  static constexpr int T2 = 256;  // phase-2 threads
+  static constexpr int W = T1 * P / N1;        // phase-1 columns per tile
+  static constexpr int U = T2 * P / (2 * N2);  // phase-2 units per tile
+  static constexpr int UPS = N1 / 2;           // units per pair-segment
+  static constexpr int SLOTS = U > UPS ? U / UPS : 1;  // segments in flight per phase-2 tile
+  static constexpr int NUB = U > UPS ? 1 : UPS / U;    // unit blocks per pair-segment
+  static constexpr int PP = P / (2 * Q2);              // p-values per thread after the joint transpose
+  static constexpr int NACC = P / 2;                   // accumulator slots (bins) per phase-2 thread
+  static constexpr int NATIVE = UPS * N2 + 1;          // native accumulator bins per FFT pair (= N/2 + 1)
+  static constexpr int S1_LD = W + 1;                  // padded row of the phase-1 transpose buffer
+  static constexpr int S2_LD = 2 * U + 1;              // padded row of the phase-2 transpose buffer
+  static constexpr size_t SMEM1 = sizeof(float2) * (size_t)Q1 * P * S1_LD;
+  static constexpr size_t SMEM2 = sizeof(float2) * ((size_t)Q2 * P * S2_LD + (size_t)SLOTS * 2 * N2);
+  static_assert(N1 * N2 == N, "plan");
+  static_assert(Q1 >= 1 && Q1 <= P && Q2 >= 1 && 2 * Q2 <= P, "plan bounds");
+  static_assert(W >= 1 && U >= 1 && T1 % W == 0 && T2 % (2 * U) == 0, "tiles");
+  static_assert(UPS % U == 0 || U % UPS == 0, "units");
+  static_assert(N1 <= 1024 && N2 <= 1024, "constant twiddle table covers L <= 1024");
+};
+
+}  // namespace polaris

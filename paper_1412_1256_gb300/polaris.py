@@ -1,0 +1,218 @@
+"""Thin ctypes binding over ``libpolaris.so`` (C ABI in ``include/polaris.h``).
+
+Argument marshalling only: every step of the hot path (data translation,
+windowing, FFT, correlation, accumulation, Stokes) runs in the library's CUDA
+kernels.  Host inputs are numpy arrays; device inputs and outputs are torch CUDA
+tensors (PyTorch provides device memory and streams, nothing else).  There is
+no fallback: if the library is missing or cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpolaris.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT = 0, -1, -2, -3, -4, -5
+WIN_RECT, WIN_HANN, WIN_CUSTOM = 0, 1, 2
+FEED_LINEAR, FEED_CIRCULAR = 0, 1
+STATUS_NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ESTATE: "ESTATE", ETIMEOUT: "ETIMEOUT"}
+
+EXPORTS = (
+    "spectrometer_create", "spectrometer_feed", "spectrometer_integrate", "spectrometer_integrate_device",
+    "spectrometer_n_bins", "spectrometer_n_pairs", "spectrometer_debug_unpack", "spectrometer_destroy",
+    "spectrometer_last_error", "polaris_set_alloc_limit",
+)
+
+
+class PolarisError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class polaris_config(ctypes.Structure):
+    _fields_ = [
+        ("n_if", ctypes.c_int), ("bits", ctypes.c_int), ("n_fft", ctypes.c_int64), ("hop", ctypes.c_int64),
+        ("window", ctypes.c_int), ("taps", ctypes.POINTER(ctypes.c_float)), ("n_pair", ctypes.c_int),
+        ("pairs", ctypes.POINTER(ctypes.c_int)), ("accum_fp64", ctypes.c_int), ("device", ctypes.c_int),
+        ("max_batch_segments", ctypes.c_int),
+    ]
+
+
+class polaris_stokes_params(ctypes.Structure):
+    _fields_ = [("feed", ctypes.c_int), ("psi_m", ctypes.c_double), ("gains", ctypes.POINTER(ctypes.c_float))]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH):
+    """Load libpolaris.so (raises if it is absent: there is no CPU fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                raise FileNotFoundError(f"{path} not built; run __graft_entry__.build()")
+            lib = ctypes.CDLL(path)
+            vp, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+            lib.spectrometer_create.argtypes = [ctypes.POINTER(polaris_config), ctypes.POINTER(vp)]
+            lib.spectrometer_create.restype = ci
+            lib.spectrometer_feed.argtypes = [vp, ctypes.POINTER(vp), i64, ci, vp]
+            lib.spectrometer_feed.restype = ci
+            lib.spectrometer_integrate.argtypes = [vp, ctypes.POINTER(polaris_stokes_params), vp, vp, vp,
+                                                   ctypes.POINTER(i64)]
+            lib.spectrometer_integrate.restype = ci
+            lib.spectrometer_integrate_device.argtypes = [vp, ctypes.POINTER(polaris_stokes_params), vp, vp, vp,
+                                                          ctypes.POINTER(i64), vp]
+            lib.spectrometer_integrate_device.restype = ci
+            lib.spectrometer_n_bins.argtypes = [vp]
+            lib.spectrometer_n_bins.restype = i64
+            lib.spectrometer_n_pairs.argtypes = [vp]
+            lib.spectrometer_n_pairs.restype = ci
+            lib.spectrometer_debug_unpack.argtypes = [vp, vp, i64, vp]
+            lib.spectrometer_debug_unpack.restype = ci
+            lib.spectrometer_destroy.argtypes = [vp]
+            lib.spectrometer_destroy.restype = None
+            lib.spectrometer_last_error.argtypes = [vp]
+            lib.spectrometer_last_error.restype = ctypes.c_char_p
+            lib.polaris_set_alloc_limit.argtypes = [i64]
+            lib.polaris_set_alloc_limit.restype = None
+            _lib = lib
+    return _lib
+
+
+def set_alloc_limit(nbytes: int) -> None:
+    load().polaris_set_alloc_limit(int(nbytes))
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _ptr(x):
+    """Address of a numpy array or torch tensor (host or device)."""
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x.data_ptr())
+
+
+class Spectrometer:
+    """One spectrometer handle.  Mirrors spectrometer_create / feed / integrate / destroy."""
+
+    def __init__(self, n_if: int, bits: int, n_fft: int, hop: int = 0, window="rect", pairs=None,
+                 accum_fp64: bool = False, device: int = 0, max_batch_segments: int = 0):
+        lib = load()
+        cfg = polaris_config()
+        cfg.n_if, cfg.bits, cfg.n_fft, cfg.hop = n_if, bits, n_fft, hop
+        self._taps = None
+        if isinstance(window, str):
+            cfg.window = {"rect": WIN_RECT, "hann": WIN_HANN}[window]
+        elif isinstance(window, int):
+            cfg.window = window
+        else:
+            self._taps = np.ascontiguousarray(window, dtype=np.float32)
+            cfg.window = WIN_CUSTOM
+            cfg.taps = self._taps.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        self._pairs = None
+        if pairs is not None:
+            self._pairs = np.ascontiguousarray(np.array(pairs, dtype=np.int32).reshape(-1))
+            cfg.n_pair = len(self._pairs) // 2
+            cfg.pairs = self._pairs.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+        cfg.accum_fp64 = int(bool(accum_fp64))
+        cfg.device = device
+        cfg.max_batch_segments = max_batch_segments
+        h = ctypes.c_void_p()
+        rc = lib.spectrometer_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc != OK:
+            raise PolarisError(rc, lib.spectrometer_last_error(None).decode())
+        self._h = h
+        self.n_if, self.bits, self.n_fft = n_if, bits, n_fft
+        self.n_bins = int(lib.spectrometer_n_bins(h))
+        self.n_pairs = int(lib.spectrometer_n_pairs(h))
+        self.device = device
+
+    def _check(self, rc):
+        if rc != OK:
+            raise PolarisError(rc, load().spectrometer_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().spectrometer_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def feed(self, packed, n_samples: int, on_device: bool | None = None, stream=None) -> None:
+        """packed: one array/tensor of uint32 words per IF (numpy -> host, torch CUDA -> device)."""
+        if on_device is None:
+            on_device = not isinstance(packed[0], np.ndarray)
+        if not on_device:
+            packed = [np.ascontiguousarray(p, dtype=np.uint32) for p in packed]
+        arr = (ctypes.c_void_p * self.n_if)(*[_ptr(p) for p in packed])
+        self._keep = packed
+        self._check(load().spectrometer_feed(self._h, arr, int(n_samples), int(bool(on_device)),
+                                             _stream_ptr(stream)))
+
+    @staticmethod
+    def _params(feed: int, psi: float, gains):
+        p = polaris_stokes_params()
+        p.feed, p.psi_m = feed, psi
+        g = None
+        if gains is not None:
+            g = np.ascontiguousarray(np.array([[complex(a).real, complex(a).imag, complex(b).real, complex(b).imag]
+                                               for a, b in gains], dtype=np.float32).reshape(-1))
+            p.gains = g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+        return p, g
+
+    def integrate(self, feed: int = FEED_LINEAR, psi: float = 0.0, gains=None):
+        """Close the integration; returns dict(autos, cross (complex), stokes, n_segments) as numpy."""
+        nb, npair = self.n_bins, self.n_pairs
+        autos = np.empty((self.n_if, nb), np.float32)
+        cross = np.empty((max(npair, 1), nb, 2), np.float32)
+        stokes = np.empty((max(npair, 1), 4, nb), np.float32)
+        nseg = ctypes.c_int64(0)
+        p, g = self._params(feed, psi, gains)
+        self._check(load().spectrometer_integrate(self._h, ctypes.byref(p), autos.ctypes.data, cross.ctypes.data,
+                                                  stokes.ctypes.data, ctypes.byref(nseg)))
+        del g
+        cross = cross[:npair]
+        return {"autos": autos, "cross": cross[..., 0] + 1j * cross[..., 1], "stokes": stokes[:npair],
+                "n_segments": int(nseg.value)}
+
+    def integrate_device(self, autos, cross, stokes, feed: int = FEED_LINEAR, psi: float = 0.0, gains=None,
+                         stream=None) -> int:
+        """Outputs into device tensors (float32: autos [n_if, nb], cross [n_pair, nb, 2],
+        stokes [n_pair, 4, nb]; None skips).  Returns the segment count."""
+        nseg = ctypes.c_int64(0)
+        p, g = self._params(feed, psi, gains)
+        self._check(load().spectrometer_integrate_device(
+            self._h, ctypes.byref(p), None if autos is None else _ptr(autos), None if cross is None else _ptr(cross),
+            None if stokes is None else _ptr(stokes), ctypes.byref(nseg), _stream_ptr(stream)))
+        del g
+        return int(nseg.value)
+
+    def debug_unpack(self, words: np.ndarray, n: int) -> np.ndarray:
+        w = np.ascontiguousarray(words, dtype=np.uint32)
+        out = np.empty(max(n, 1), np.float32)
+        self._check(load().spectrometer_debug_unpack(self._h, w.ctypes.data, int(n), out.ctypes.data))
+        return out[:n]

@@ -1,0 +1,180 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bar: unpacking bit-exact; spectra and Stokes within 1e-5 max relative error per
+channel (normalisation in tests/helpers.py) for the FP32 path.
+"""
+import numpy as np
+import pytest
+
+from paper_1412_1256_gb300 import synth
+from tests.helpers import assert_close
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def pol():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1412_1256_gb300 import polaris
+
+    polaris.load()
+    return polaris
+
+
+def _run(pol, packed, bits, n_fft, n, hop=0, window="rect", pairs=None, chunks=None, **kw):
+    n_if = len(packed)
+    with pol.Spectrometer(n_if, bits, n_fft, hop=hop, window=window, pairs=pairs, **kw) as sp:
+        if chunks is None:
+            sp.feed(packed, n)
+        else:
+            spw = 32 // bits
+            pos = 0
+            for c in chunks:
+                w0, w1 = pos // spw, (pos + c) // spw
+                sp.feed([p[w0:w1] for p in packed], c)
+                pos += c
+        return sp.integrate()
+
+
+def _oracle(orc, packed, bits, n_fft, n, hop=None, window_kind=0, taps=None, pairs=None):
+    return orc.spectrometer(packed, bits, n_fft, n, hop=hop, window_kind=window_kind, taps=taps, pairs=pairs)
+
+
+def _random_streams(seed, n_if, n, bits):
+    rng = np.random.default_rng(seed)
+    return [synth.pack(synth.random_codes(rng, n, bits), bits) for _ in range(n_if)]
+
+
+def test_tiny_config_hann_int8(pol, orc):
+    packed, meta = synth.config_tiny()
+    n = meta["n_samples"]
+    got = _run(pol, packed, 8, 1024, n, window="hann")
+    ref = _oracle(orc, packed, 8, 1024, n, window_kind=1)
+    assert got["n_segments"] == ref["n_segments"] == 64
+    assert_close(got, ref, [(0, 1)], TOL)
+
+
+@pytest.mark.parametrize("logn", list(range(4, 19)))
+def test_sizes_two_pairs_2bit(pol, orc, logn):
+    n_fft = 1 << logn
+    nseg = 8 if logn >= 15 else 24
+    n = nseg * n_fft
+    packed = _random_streams(logn, 4, n, 2)
+    got = _run(pol, packed, 2, n_fft, n)
+    ref = _oracle(orc, packed, 2, n_fft, n)
+    assert got["n_segments"] == nseg
+    assert_close(got, ref, [(0, 2), (1, 3)], TOL)
+
+
+@pytest.mark.parametrize("bits", [1, 2, 4, 8])
+def test_bits(pol, orc, bits):
+    n_fft, nseg = 4096, 16
+    n = n_fft * nseg
+    packed = _random_streams(100 + bits, 2, n, bits)
+    got = _run(pol, packed, bits, n_fft, n)
+    ref = _oracle(orc, packed, bits, n_fft, n)
+    assert_close(got, ref, [(0, 1)], TOL)
+
+
+def test_paper_config_one_integration(pol, orc):
+    """4 IFs, 2-bit, N = 131072, 61 segments (one 1-s integration), three-line spectrum."""
+    packed, meta = synth.config_paper(n_segments=61)
+    n = meta["n_samples"]
+    got = _run(pol, packed, 2, 131072, n)
+    ref = _oracle(orc, packed, 2, 131072, n)
+    assert got["n_segments"] == 61
+    assert_close(got, ref, [(0, 2), (1, 3)], TOL)
+
+
+def test_overlap_and_ragged_feeds(pol, orc):
+    """50% overlap (Sec. 3.1) and a stream fed in uneven pieces: carry-over of partial segments."""
+    n_fft, bits = 2048, 2
+    n = 2048 * 20 + 512
+    packed = _random_streams(7, 4, n, bits)
+    chunks = [1024, 4096, 16, 7168, 2048 * 5, n - (1024 + 4096 + 16 + 7168 + 2048 * 5)]
+    got = _run(pol, packed, bits, n_fft, n, hop=1024, chunks=chunks)
+    ref = _oracle(orc, packed, bits, n_fft, n, hop=1024)
+    assert got["n_segments"] == ref["n_segments"]
+    assert_close(got, ref, [(0, 2), (1, 3)], TOL)
+
+
+def test_custom_taps_fp64_accum(pol, orc):
+    n_fft, nseg = 16384, 12
+    n = n_fft * nseg
+    rng = np.random.default_rng(5)
+    taps = rng.uniform(0.2, 1.0, n_fft).astype(np.float32)
+    packed = _random_streams(9, 2, n, 8)
+    got = _run(pol, packed, 8, n_fft, n, window=taps, accum_fp64=True)
+    ref = _oracle(orc, packed, 8, n_fft, n, window_kind=2, taps=taps)
+    assert_close(got, ref, [(0, 1)], TOL)
+
+
+@pytest.mark.parametrize("n_if,pairs", [(1, None), (3, None), (3, [(2, 0)]), (6, None), (8, [(7, 0), (3, 4)])])
+def test_if_counts_and_pairs(pol, orc, n_if, pairs):
+    n_fft, nseg = 1024, 20
+    n = n_fft * nseg
+    packed = _random_streams(11 + n_if, n_if, n, 4)
+    got = _run(pol, packed, 4, n_fft, n, pairs=pairs)
+    ref = _oracle(orc, packed, 4, n_fft, n, pairs=pairs)
+    ps = orc.default_pairs(n_if) if pairs is None else pairs
+    assert_close(got, ref, ps, TOL)
+
+
+@pytest.mark.parametrize("feed,psi", [(0, 0.3), (1, -0.7)])
+def test_stokes_params(pol, orc, feed, psi):
+    packed, meta = synth.config_tiny()
+    n = meta["n_samples"]
+    gains = [(1.2 - 0.3j, 0.8 + 0.1j)]
+    with pol.Spectrometer(2, 8, 1024, window="hann") as sp:
+        sp.feed(packed, n)
+        got = sp.integrate(feed=feed, psi=psi, gains=gains)
+    ref = orc.spectrometer(packed, 8, 1024, n, window_kind=1, feed=feed, psi=psi, gains=gains)
+    assert_close(got, ref, [(0, 1)], TOL)
+
+
+@pytest.mark.parametrize("bits", [1, 2, 4, 8])
+def test_unpack_bit_exact_every_code(pol, orc, bits):
+    rng = np.random.default_rng(bits)
+    spw = 32 // bits
+    codes = np.concatenate([np.tile(np.arange(1 << bits), max(1, 64 // (1 << bits))),
+                            synth.random_codes(rng, 4096, bits)])
+    codes = codes[: len(codes) - len(codes) % spw]
+    words = synth.pack(codes, bits)
+    with pol.Spectrometer(1, bits, 1024) as sp:
+        got = sp.debug_unpack(words, len(codes))
+    ref = orc.decode(bits, words, len(codes))
+    assert np.array_equal(got.astype(np.float64), ref)
+
+
+def test_integrate_without_segments_is_state_error(pol):
+    with pol.Spectrometer(2, 2, 1024) as sp:
+        with pytest.raises(pol.PolarisError) as ei:
+            sp.integrate()
+        assert ei.value.code == pol.ESTATE
+        sp.feed([np.zeros(32, np.uint32)] * 2, 512)  # less than one segment: still nothing
+        with pytest.raises(pol.PolarisError):
+            sp.integrate()
+
+
+def test_invalid_configs(pol):
+    for kw in [dict(n_if=0, bits=2, n_fft=1024), dict(n_if=2, bits=3, n_fft=1024), dict(n_if=2, bits=2, n_fft=1000),
+               dict(n_if=2, bits=2, n_fft=1024, hop=8), dict(n_if=2, bits=2, n_fft=1024, pairs=[(0, 0)]),
+               dict(n_if=2, bits=1, n_fft=16)]:
+        with pytest.raises(pol.PolarisError) as ei:
+            pol.Spectrometer(**kw)
+        assert ei.value.code == pol.EINVAL
+
+
+def test_alloc_limit_gives_enomem(pol):
+    pol.set_alloc_limit(1 << 20)
+    try:
+        with pytest.raises(pol.PolarisError) as ei:
+            pol.Spectrometer(4, 2, 131072)
+        assert ei.value.code == pol.ENOMEM
+    finally:
+        pol.set_alloc_limit(-1)
+    with pol.Spectrometer(4, 2, 1024):
+        pass
