@@ -1,0 +1,426 @@
+"""Throughput benchmark of the PolariS hot path on GB300.
+
+Workload (one "step" = one pass of the whole path over one batch): one 1-s
+integration of the paper-shaped load - 4 IF streams (X0, X1, Y0, Y1), 2-bit
+samples, 131072-point real FFT segments, 61 segments per IF (8 Msps), autos,
+crosses and Stokes I, Q, U, V of both pairs - i.e. 4 x 61 x 131072 =
+31,981,568 input samples per step.
+
+  value  device-resident input (a 480 MB ring of distinct seconds, larger than
+         L2, so every step reads its input from HBM), feed + integrate to device
+         outputs through the C ABI, timed with CUDA events on the launching stream.
+  e2e    the same metric through the C ABI with pinned HOST buffers: host->device
+         copy of the step's packed input and device->host copy of its autos,
+         crosses and Stokes inside the timed region.
+
+--impl reference times the FP64 CPU oracle on this machine's host cores on a
+bounded sample of the same workload (the reference arm; there is no upstream code).
+
+Multi-GPU (torchrun): the path does not need any exchange between GPUs, so each
+rank runs an independent replica on its own GPU and data; value sums all ranks'
+samples over the slowest rank's time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import ctypes.util
+import hashlib
+import glob
+import json
+import math
+import os
+import statistics
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "input Msample/s through unpack+FFT+correlate at 2^17 pt; fraction of roofline"
+N_IF, BITS, N_FFT, SEGS = 4, 2, 131072, 61
+SAMPLES_PER_IF = SEGS * N_FFT
+SAMPLES_PER_STEP = N_IF * SAMPLES_PER_IF
+WORDS_PER_IF = SAMPLES_PER_IF * BITS // 32
+NBIN = N_FFT // 2 + 1
+N_PAIR = 2
+D2H_BYTES = NBIN * 4 * N_IF + NBIN * 8 * N_PAIR + NBIN * 16 * N_PAIR
+H2D_BYTES = N_IF * WORDS_PER_IF * 4
+CONFIG = {
+    "workload": "4 IF x 2-bit x 131072-pt R2C FFT, 61 segments per IF = one 1-s integration at 8 Msps per step; "
+                "4 autos + 2 complex crosses + Stokes I,Q,U,V (rectangular window)",
+    "n_if": N_IF, "bits": BITS, "n_fft": N_FFT, "segments_per_integration": SEGS, "integrations_per_step": 1,
+    "samples_per_step": SAMPLES_PER_STEP,
+    "l2": "inputs larger than L2: 60 distinct seconds (480 MB ring) cycled, each step reads another second",
+}
+
+
+# ------------------------------------------------------------------------------------------
+# algorithmic work (flops) per step, split by kernel
+# ------------------------------------------------------------------------------------------
+def algorithmic_flops():
+    """Nominal flop counts: FFT 5 N log2 N / 2 per real segment (split between the two
+    kernels by their radix stages: log2 N1 = 8 rows, log2 N2 = 9 columns), correlate
+    32 flop per bin per segment-time for the four autos and two crosses, window 1 flop
+    per sample."""
+    segs = N_IF * SEGS
+    fft_stage = segs * 5.0 * N_FFT / 2.0  # one radix-2 stage of all real segments
+    n1_log, n2_log = 8, 9
+    corr = SEGS * NBIN * 32.0
+    window = float(SAMPLES_PER_STEP)
+    return {
+        "phase1_decode_rowdft": fft_stage * n1_log + window,
+        "phase2_coldft_correlate": fft_stage * n2_log + corr,
+        "readout_stokes": 0.0,
+        "path": fft_stage * math.log2(N_FFT) + corr + window,
+    }
+
+
+def fp32_peak_tflops(num_sms: int, sm_mhz: float) -> float:
+    """CUDA-core FP32 peak: SMs x 128 FP32 lanes x 2 flop (FMA) x clock."""
+    return num_sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def source_digest() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1412_1256_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from a committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        parts = line.split()
+        if len(parts) == 2 and not line.startswith("#"):
+            vals[parts[0]] = parts[1]
+    if vals.get("source_digest") != source_digest():
+        return None
+    try:
+        return float(vals["dram_bytes_per_segment_pair"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------------------------------
+# clocks: read-only NVML queries in a sampling thread
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    REASONS = {0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+               0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
+
+    def __init__(self, cuda_index: int, period_s: float = 0.002):
+        self.samples, self.reasons, self.max_mhz = [], 0, None
+        self.period, self._stop = period_s, threading.Event()
+        self.ok = False
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                return
+            # map the CUDA ordinal to the NVML one when CUDA_VISIBLE_DEVICES renumbers devices
+            index = cuda_index
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            if vis:
+                ids = [v.strip() for v in vis.split(",") if v.strip()]
+                if cuda_index < len(ids) and ids[cuda_index].isdigit():
+                    index = int(ids[cuda_index])
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)) != 0:
+                return
+            self.reason_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons", None)
+            self.lib, self.h = lib, h
+            mx = ctypes.c_uint()
+            if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+                self.max_mhz = mx.value
+            self.ok = True
+        except OSError:
+            pass
+
+    def _run(self):
+        c = ctypes.c_uint()
+        r = ctypes.c_ulonglong()
+        while not self._stop.is_set():
+            if self.lib.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(c)) == 0:
+                self.samples.append(c.value)
+            if self.reason_fn is not None and self.reason_fn(self.h, ctypes.byref(r)) == 0:
+                self.reasons |= r.value
+            time.sleep(self.period)
+
+    def __enter__(self):
+        if self.ok:
+            self.t = threading.Thread(target=self._run, daemon=True)
+            self.t.start()
+        return self
+
+    def __exit__(self, *a):
+        if self.ok:
+            self._stop.set()
+            self.t.join()
+
+    def summary(self):
+        if not self.ok or not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": ["unavailable"], "samples": 0}
+        names = [n for b, n in self.REASONS.items() if self.reasons & b and n != "gpu_idle"]
+        return {"sm_mhz": float(statistics.median(self.samples)), "sm_max_mhz": self.max_mhz, "reasons": names,
+                "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------------------------------
+# inputs
+# ------------------------------------------------------------------------------------------
+def make_unique_seconds(n_unique: int):
+    from paper_1412_1256_gb300 import synth
+
+    out = []
+    for i in range(n_unique):
+        packed, meta = synth.config_paper(seed=1256 + i, n_segments=SEGS, n_fft=N_FFT, n_if=N_IF, bits=BITS)
+        out.append(np.stack(packed).view(np.int32))  # [N_IF, WORDS_PER_IF]
+    return out
+
+
+# ------------------------------------------------------------------------------------------
+# CPU baseline / reference arm: the FP64 oracle on a bounded sample
+# ------------------------------------------------------------------------------------------
+def time_oracle(unique, segs: int, repeats: int = 1):
+    """Time the FP64 oracle on `segs` segments of one integration (4 IF), `repeats` times."""
+    import oracle
+
+    oracle.build()
+    u = unique[0].view(np.uint32)
+    n = segs * N_FFT
+    packed = [np.ascontiguousarray(u[i, : n * BITS // 32]) for i in range(N_IF)]
+    t0 = time.perf_counter()
+    for _ in range(repeats):
+        oracle.spectrometer(packed, BITS, N_FFT, n)
+    dt = time.perf_counter() - t0
+    return repeats * N_IF * n / dt / 1e6, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    unique = make_unique_seconds(1)
+    # size the per-step sample so that warmup + steps take about a minute
+    _, t1 = time_oracle(unique, 1)
+    budget = 60.0 / max(1, args.steps + args.warmup)
+    segs = int(max(1, min(SEGS, budget / max(t1, 1e-3))))
+    for _ in range(args.warmup):
+        time_oracle(unique, segs)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        time_oracle(unique, segs)
+    dt = time.perf_counter() - t0
+    value = args.steps * N_IF * segs * N_FFT / dt / 1e6
+    sample = f"{segs} of the 61 segments of one integration per step (4 IF x {segs} x 131072 samples), FP64 oracle"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Msample/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": CONFIG,
+        "cpu_baseline": {"value": value, "unit": "Msample/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Msample/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank, dist):
+    import torch
+
+    from paper_1412_1256_gb300 import polaris
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    polaris.load()
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    unique = make_unique_seconds(args.unique)
+    ring_n = args.ring
+    ring = torch.empty((ring_n, N_IF, WORDS_PER_IF), dtype=torch.int32, device=dev)
+    for i in range(ring_n):
+        ring[i].copy_(torch.from_numpy(unique[i % len(unique)]))
+    autos = torch.empty((N_IF, NBIN), dtype=torch.float32, device=dev)
+    cross = torch.empty((N_PAIR, NBIN, 2), dtype=torch.float32, device=dev)
+    stokes = torch.empty((N_PAIR, 4, NBIN), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = polaris.Spectrometer(N_IF, BITS, N_FFT, device=local_rank)
+
+    def step(i):
+        sec = ring[i % ring_n]
+        sp.feed([sec[j] for j in range(N_IF)], SAMPLES_PER_IF, on_device=True, stream=stream)
+        return sp.integrate_device(autos, cross, stokes, stream=stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for i in range(args.warmup):
+        assert step(i) == SEGS
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    l0 = sp.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        e0.record(stream)
+        for i in range(args.steps):
+            step(args.warmup + i)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    launches = sp.kernel_launches() - l0
+    t_ms = e0.elapsed_time(e1)
+    t_max = t_ms
+    if dist is not None:
+        tt = torch.tensor([t_ms], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * args.steps * SAMPLES_PER_STEP / (t_max * 1e-3) / 1e6
+
+    # per-kernel device time: a second timed pass with every launch bracketed by events
+    sp.set_profiling(True)
+    prof_steps = max(3, min(args.steps, 50))
+    for i in range(prof_steps):
+        step(i)
+    torch.cuda.synchronize(dev)
+    kt = sp.kernel_times()
+    sp.set_profiling(False)
+
+    # e2e through the C ABI with pinned host buffers
+    e2e_value = None
+    if not args.no_e2e:
+        n_host = min(len(unique), 4)
+        pinned = [torch.from_numpy(unique[i]).pin_memory() for i in range(n_host)]
+        host = [p.numpy().view(np.uint32) for p in pinned]
+        for i in range(2):
+            sp.feed([host[i % n_host][j] for j in range(N_IF)], SAMPLES_PER_IF, on_device=False)
+            sp.integrate()
+        e2e_steps = max(3, min(args.steps, args.e2e_steps))
+        torch.cuda.synchronize(dev)
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            sp.feed([host[i % n_host][j] for j in range(N_IF)], SAMPLES_PER_IF, on_device=False)
+            out = sp.integrate()
+            assert out["n_segments"] == SEGS
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        if dist is not None:
+            tt = torch.tensor([dt], dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
+        e2e_value = world * e2e_steps * SAMPLES_PER_STEP / dt / 1e6
+
+    sp.close()
+    if rank != 0:
+        return
+
+    flops = algorithmic_flops()
+    clocks = clk.summary()
+    peak_mhz = float(clocks["sm_max_mhz"] or 2070.0)
+    peak = fp32_peak_tflops(num_sms, peak_mhz)
+    kernels = {}
+    total_kt = sum(v[0] for v in kt.values()) or 1.0
+    for k, (ms, n) in kt.items():
+        if n:
+            per_step = flops[k]  # flops per step for this kernel
+            launches_per_step = n / prof_steps
+            kernels[k] = {"avg_ms": ms / n, "launches": n, "share": ms / total_kt,
+                          "tflops": (per_step * prof_steps / (ms * 1e-3) / 1e12) if ms > 0 and per_step else 0.0,
+                          "launches_per_step": launches_per_step}
+    dom = max(kernels, key=lambda k: kernels[k]["avg_ms"] * kernels[k]["launches"])
+    ach = kernels[dom]["tflops"]
+    traffic = recorded_traffic(dom)
+    if traffic is not None:
+        # bytes per launch: per-segment-pair figure x pair-segments per launch
+        traffic = traffic * (N_PAIR * SEGS) / kernels[dom]["launches_per_step"]
+    path_tflops = flops["path"] * args.steps / (t_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "Msample/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic: seeded 4-IF 2-bit streams, Gaussian noise + three Gaussian lines (FWHM 20 ch, 5x "
+                "continuum; unpolarised, linear, circular)",
+        "config": CONFIG,
+        "roofline": {
+            "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": traffic, "kernel": dom,
+            "peak_source": f"derived: {num_sms} SMs x 128 FP32 lanes x 2 flop x {peak_mhz:.0f} MHz (max SM clock)",
+        },
+        "path_roofline": {
+            "achieved": path_tflops, "peak": peak, "unit": "TFLOP/s", "frac": path_tflops / peak,
+            "roofline_msample_s": peak * 1e12 / (flops["path"] / SAMPLES_PER_STEP) / 1e6,
+            "note": "whole step (all kernels, launch gaps included) against the FP32 roofline",
+        },
+        "kernels": kernels,
+        "e2e": {"value": e2e_value, "unit": "Msample/s", "h2d_bytes_per_step": H2D_BYTES,
+                "d2h_bytes_per_step": D2H_BYTES},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        v, dt = time_oracle(unique, args.cpu_segs, args.cpu_repeats)
+        line["cpu_baseline"] = {"value": v, "unit": "Msample/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{args.cpu_repeats} x {args.cpu_segs} segments of one integration "
+                                          f"(4 IF x 131072-sample segments), single-threaded FP64 oracle, {dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ring", type=int, default=60, help="distinct seconds of input kept on the device")
+    ap.add_argument("--unique", type=int, default=2, help="distinct generated seconds (tiled over the ring)")
+    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--cpu-segs", type=int, default=61)
+    ap.add_argument("--cpu-repeats", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist_mod.init_process_group("gloo", rank=rank, world_size=world)
+        dist = dist_mod
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank)
+        else:
+            run_ours(args, rank, world, local_rank, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -152,6 +152,17 @@ void spectrometer_destroy(polaris_spec* s);
  * error of a failed spectrometer_create in this thread. */
 const char* spectrometer_last_error(const polaris_spec* s);
 
+/* Kernel accounting (for benchmarks).  spectrometer_kernel_launches: kernels this
+ * handle has launched so far, all kinds.  spectrometer_set_profiling(s, 1) brackets
+ * every later launch with CUDA events on its stream; spectrometer_kernel_times then
+ * waits for those events and returns, per kind, the summed device time in ms and the
+ * launch count since profiling began or since the previous query (kinds: 0 = phase 1,
+ * decode/window/row DFT; 1 = phase 2, column DFT/correlate/accumulate; 2 = readout and
+ * Stokes).  n is the length of both arrays and must be >= 3. */
+int64_t spectrometer_kernel_launches(const polaris_spec* s);
+int spectrometer_set_profiling(polaris_spec* s, int on);
+int spectrometer_kernel_times(polaris_spec* s, double* ms, int64_t* launches, int n);
+
 /* Test hook: cap the bytes of device memory that later spectrometer_create
  * calls may allocate (-1 = no cap), so that allocation failure can be tested
  * without exhausting the GPU. */

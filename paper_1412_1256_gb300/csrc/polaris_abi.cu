@@ -15,8 +15,10 @@
 #include "polaris_kernels.cuh"
 
 namespace polaris {
-// per-size batch runners, one translation unit each (polaris_n<LOGN>.cu)
-#define POLARIS_DECLARE(LOGN) extern template cudaError_t run_batch<LOGN>(const BatchArgs&, cudaStream_t);
+// per-size phase runners, one translation unit each (polaris_n<LOGN>.cu)
+#define POLARIS_DECLARE(LOGN)                                                    \
+  extern template cudaError_t run_phase1<LOGN>(const BatchArgs&, cudaStream_t); \
+  extern template cudaError_t run_phase2<LOGN>(const BatchArgs&, cudaStream_t);
 POLARIS_DECLARE(4)
 POLARIS_DECLARE(5)
 POLARIS_DECLARE(6)
@@ -35,27 +37,14 @@ POLARIS_DECLARE(18)
 POLARIS_DECLARE(19)
 #undef POLARIS_DECLARE
 
-static cudaError_t dispatch_batch(int logn, const BatchArgs& a, cudaStream_t st) {
-  switch (logn) {
-    case 4: return run_batch<4>(a, st);
-    case 5: return run_batch<5>(a, st);
-    case 6: return run_batch<6>(a, st);
-    case 7: return run_batch<7>(a, st);
-    case 8: return run_batch<8>(a, st);
-    case 9: return run_batch<9>(a, st);
-    case 10: return run_batch<10>(a, st);
-    case 11: return run_batch<11>(a, st);
-    case 12: return run_batch<12>(a, st);
-    case 13: return run_batch<13>(a, st);
-    case 14: return run_batch<14>(a, st);
-    case 15: return run_batch<15>(a, st);
-    case 16: return run_batch<16>(a, st);
-    case 17: return run_batch<17>(a, st);
-    case 18: return run_batch<18>(a, st);
-    case 19: return run_batch<19>(a, st);
-    default: return cudaErrorInvalidValue;
-  }
-}
+typedef cudaError_t (*phase_fn)(const BatchArgs&, cudaStream_t);
+#define POLARIS_ROW(LOGN) {run_phase1<LOGN>, run_phase2<LOGN>}
+static const phase_fn kPhases[20][2] = {
+    {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr},
+    POLARIS_ROW(4),  POLARIS_ROW(5),  POLARIS_ROW(6),  POLARIS_ROW(7),  POLARIS_ROW(8),  POLARIS_ROW(9),
+    POLARIS_ROW(10), POLARIS_ROW(11), POLARIS_ROW(12), POLARIS_ROW(13), POLARIS_ROW(14), POLARIS_ROW(15),
+    POLARIS_ROW(16), POLARIS_ROW(17), POLARIS_ROW(18), POLARIS_ROW(19)};
+#undef POLARIS_ROW
 
 // ---------------------------------------------------------------------------------------
 // data translation alone
@@ -186,6 +175,14 @@ struct polaris_spec {
   float* d_out_stokes = nullptr;
   cudaEvent_t ev_h2d = nullptr;
   int64_t seg_acc = 0;  // segments accumulated in the open integration
+  int64_t launches = 0; // kernels launched by this handle (all kinds)
+  bool profiling = false;
+  struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<ProfRec> prof;      // bracketed launches not yet summed
+  std::vector<cudaEvent_t> spare; // event pool
   bool broken = false;
   std::string err;
 };
@@ -226,7 +223,53 @@ struct DeviceGuard {
   }
 };
 
+static void drop_prof(polaris_spec* s) {
+  for (auto& r : s->prof) {
+    s->spare.push_back(r.a);
+    s->spare.push_back(r.b);
+  }
+  s->prof.clear();
+}
+
+static cudaEvent_t take_event(polaris_spec* s) {
+  if (!s->spare.empty()) {
+    cudaEvent_t e = s->spare.back();
+    s->spare.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Launch one kernel through `fn`, counting it and, when profiling, bracketing it with
+// CUDA events on the launching stream.  kind: 0 phase 1, 1 phase 2, 2 readout.
+template <typename F>
+static cudaError_t counted_launch(polaris_spec* s, int kind, cudaStream_t st, F&& fn) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (s->profiling) {
+    a = take_event(s);
+    b = take_event(s);
+    if (a) cudaEventRecord(a, st);
+  }
+  cudaError_t e = fn();
+  if (e == cudaSuccess) ++s->launches;
+  if (s->profiling) {
+    if (a && b && e == cudaSuccess) {
+      cudaEventRecord(b, st);
+      s->prof.push_back({kind, a, b});
+    } else {
+      if (a) s->spare.push_back(a);
+      if (b) s->spare.push_back(b);
+    }
+  }
+  return e;
+}
+
 static void free_all(polaris_spec* s) {
+  drop_prof(s);
+  for (cudaEvent_t e : s->spare) cudaEventDestroy(e);
+  s->spare.clear();
   cudaFree(s->d_taps);
   cudaFree(s->d_tw);
   cudaFree(s->d_acc);
@@ -507,8 +550,11 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
   for (int64_t s0 = 0; s0 < nseg; s0 += s->max_batch) {
     a.seg0 = (int)s0;
     a.nseg = (int)(nseg - s0 < s->max_batch ? nseg - s0 : s->max_batch);
-    cudaError_t e = dispatch_batch(s->logn, a, st);
-    if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "FFT-correlator launch: %s", cudaGetErrorString(e));
+    for (int ph = 0; ph < 2; ++ph) {
+      const phase_fn fn = kPhases[s->logn][ph];
+      cudaError_t e = counted_launch(s, ph, st, [&]() { return fn(a, st); });
+      if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "FFT-correlator launch: %s", cudaGetErrorString(e));
+    }
   }
   // carry the samples after the last whole segment: stream positions [nseg*hop, total)
   const int64_t keep0 = nseg * hop, keep = total - keep0;
@@ -587,8 +633,10 @@ extern "C" int spectrometer_integrate_device(polaris_spec* s, const polaris_stok
   r.cross = d_cross;
   r.stokes = d_stokes;
   dim3 grid((unsigned)((s->nbin + 255) / 256), (unsigned)s->n_fpair);
-  k_readout<<<grid, 256, 0, st>>>(r);
-  CUDA_OR_FAIL(s, cudaGetLastError());
+  CUDA_OR_FAIL(s, counted_launch(s, 2, st, [&]() {
+                  k_readout<<<grid, 256, 0, st>>>(r);
+                  return cudaGetLastError();
+                }));
   const size_t acc_bytes = (size_t)s->n_fpair * s->native * 4 * (s->accum_fp64 ? 8 : 4);
   CUDA_OR_FAIL(s, cudaMemsetAsync(s->d_acc, 0, acc_bytes, st));
   if (n_segments_out) *n_segments_out = s->seg_acc;
@@ -646,5 +694,35 @@ extern "C" int spectrometer_debug_unpack(polaris_spec* s, const void* packed, in
   cudaFree(dw);
   cudaFree(df);
   if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "debug_unpack: %s", cudaGetErrorString(e));
+  return POLARIS_OK;
+}
+
+extern "C" int64_t spectrometer_kernel_launches(const polaris_spec* s) { return s ? s->launches : -1; }
+
+extern "C" int spectrometer_set_profiling(polaris_spec* s, int on) {
+  if (!s) return POLARIS_EINVAL;
+  DeviceGuard dg(s->device);
+  s->profiling = on != 0;
+  if (!s->profiling) drop_prof(s);
+  return POLARIS_OK;
+}
+
+extern "C" int spectrometer_kernel_times(polaris_spec* s, double* ms, int64_t* launches, int n) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (!ms || !launches || n < 3) return set_err(s, POLARIS_EINVAL, "need arrays of at least 3 entries");
+  DeviceGuard dg(s->device);
+  for (int k = 0; k < n; ++k) {
+    ms[k] = 0.0;
+    launches[k] = 0;
+  }
+  for (auto& r : s->prof) {
+    CUDA_OR_FAIL(s, cudaEventSynchronize(r.b));
+    float t = 0.f;
+    CUDA_OR_FAIL(s, cudaEventElapsedTime(&t, r.a, r.b));
+    ms[r.kind] += t;
+    launches[r.kind] += 1;
+  }
+  drop_prof(s);
   return POLARIS_OK;
 }

@@ -361,11 +361,13 @@ __global__ void __launch_bounds__(Plan<LOGN>::T2, 1) k_phase2(BatchArgs a, int s
 template <int LOGN, int BITS>
 static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st) {
   using PL = Plan<LOGN>;
-  static bool attr = false;
-  if (!attr) {
+  static int attr_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev != dev) {
     cudaError_t e = cudaFuncSetAttribute(k_phase1<LOGN, BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::SMEM1);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr_dev = dev;
   }
   const long long cols = (long long)a.nseg * a.n_fpair * PL::N2;
   const int grid = (int)((cols + PL::W - 1) / PL::W);
@@ -373,26 +375,32 @@ static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// phase 1 of one batch
 template <int LOGN>
-cudaError_t run_batch(const BatchArgs& a, cudaStream_t st) {
-  using PL = Plan<LOGN>;
+cudaError_t run_phase1(const BatchArgs& a, cudaStream_t st) {
   if (a.nseg <= 0) return cudaSuccess;
-  cudaError_t e;
   switch (a.bits) {
-    case 1: e = launch_phase1<LOGN, 1>(a, st); break;
-    case 2: e = launch_phase1<LOGN, 2>(a, st); break;
-    case 4: e = launch_phase1<LOGN, 4>(a, st); break;
-    case 8: e = launch_phase1<LOGN, 8>(a, st); break;
+    case 1: return launch_phase1<LOGN, 1>(a, st);
+    case 2: return launch_phase1<LOGN, 2>(a, st);
+    case 4: return launch_phase1<LOGN, 4>(a, st);
+    case 8: return launch_phase1<LOGN, 8>(a, st);
     default: return cudaErrorInvalidValue;
   }
-  if (e != cudaSuccess) return e;
-  static bool attr2 = false;
-  if (!attr2) {
-    e = cudaFuncSetAttribute(k_phase2<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::SMEM2);
+}
+
+// phase 2 of one batch: tiles = (FFT pair, unit block, chunk of segments), ~2 tiles per SM
+template <int LOGN>
+cudaError_t run_phase2(const BatchArgs& a, cudaStream_t st) {
+  using PL = Plan<LOGN>;
+  if (a.nseg <= 0) return cudaSuccess;
+  static int attr_dev = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (attr_dev != dev) {
+    cudaError_t e = cudaFuncSetAttribute(k_phase2<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::SMEM2);
     if (e != cudaSuccess) return e;
-    attr2 = true;
+    attr_dev = dev;
   }
-  // phase-2 tiles: (FFT pair, unit block, chunk of segments); aim for ~2 tiles per SM
   const int per_chunk_tiles = a.n_fpair * PL::NUB;
   const int max_chunks = (a.nseg + PL::SLOTS - 1) / PL::SLOTS;
   int want = (2 * a.num_sms + per_chunk_tiles - 1) / per_chunk_tiles;
@@ -407,5 +415,6 @@ cudaError_t run_batch(const BatchArgs& a, cudaStream_t st) {
 
 }  // namespace polaris
 
-#define POLARIS_INSTANTIATE(LOGN) \
-  template cudaError_t polaris::run_batch<LOGN>(const polaris::BatchArgs&, cudaStream_t);
+#define POLARIS_INSTANTIATE(LOGN)                                                          \
+  template cudaError_t polaris::run_phase1<LOGN>(const polaris::BatchArgs&, cudaStream_t); \
+  template cudaError_t polaris::run_phase2<LOGN>(const polaris::BatchArgs&, cudaStream_t);

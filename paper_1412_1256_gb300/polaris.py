@@ -25,7 +25,8 @@ STATUS_NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ESTATE: "EST
 EXPORTS = (
     "spectrometer_create", "spectrometer_feed", "spectrometer_integrate", "spectrometer_integrate_device",
     "spectrometer_n_bins", "spectrometer_n_pairs", "spectrometer_debug_unpack", "spectrometer_destroy",
-    "spectrometer_last_error", "polaris_set_alloc_limit",
+    "spectrometer_last_error", "polaris_set_alloc_limit", "spectrometer_kernel_launches",
+    "spectrometer_set_profiling", "spectrometer_kernel_times",
 )
 
 
@@ -81,6 +82,12 @@ def load(path: str = LIB_PATH):
             lib.spectrometer_destroy.restype = None
             lib.spectrometer_last_error.argtypes = [vp]
             lib.spectrometer_last_error.restype = ctypes.c_char_p
+            lib.spectrometer_kernel_launches.argtypes = [vp]
+            lib.spectrometer_kernel_launches.restype = i64
+            lib.spectrometer_set_profiling.argtypes = [vp, ci]
+            lib.spectrometer_set_profiling.restype = ci
+            lib.spectrometer_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), ci]
+            lib.spectrometer_kernel_times.restype = ci
             lib.polaris_set_alloc_limit.argtypes = [i64]
             lib.polaris_set_alloc_limit.restype = None
             _lib = lib
@@ -210,6 +217,21 @@ class Spectrometer:
             None if stokes is None else _ptr(stokes), ctypes.byref(nseg), _stream_ptr(stream)))
         del g
         return int(nseg.value)
+
+    def kernel_launches(self) -> int:
+        return int(load().spectrometer_kernel_launches(self._h))
+
+    def set_profiling(self, on: bool) -> None:
+        self._check(load().spectrometer_set_profiling(self._h, int(bool(on))))
+
+    KERNEL_KINDS = ("phase1_decode_rowdft", "phase2_coldft_correlate", "readout_stokes")
+
+    def kernel_times(self):
+        """{kind: (total_ms, launches)} for launches bracketed since set_profiling(True)."""
+        ms = (ctypes.c_double * 3)()
+        nl = (ctypes.c_int64 * 3)()
+        self._check(load().spectrometer_kernel_times(self._h, ms, nl, 3))
+        return {k: (ms[i], int(nl[i])) for i, k in enumerate(self.KERNEL_KINDS)}
 
     def debug_unpack(self, words: np.ndarray, n: int) -> np.ndarray:
         w = np.ascontiguousarray(words, dtype=np.uint32)
