@@ -163,6 +163,35 @@ int64_t spectrometer_kernel_launches(const polaris_spec* s);
 int spectrometer_set_profiling(polaris_spec* s, int on);
 int spectrometer_kernel_times(polaris_spec* s, double* ms, int64_t* launches, int n);
 
+/* One integration without any device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when they need a
+ * spectrum -- code running while a CUDA graph is being captured (cudaMalloc cannot be
+ * captured), real-time loops in which cudaMalloc/cudaFree would synchronise the device
+ * and miss the sampler's deadline, and host frameworks that own all device memory
+ * through their own pool.  It computes the same autos, crosses and Stokes as
+ * create + feed + integrate_device for the whole segments of one input block
+ * (samples after the last whole segment are ignored; nothing is carried), but it keeps
+ * no handle: its scratch slab, accumulators, twiddles and window taps live in one
+ * static device array of 32 MiB (POLARIS_NOALLOC_BYTES), which every GPU that loads
+ * this library holds until the process exits.
+ *   cfg         as for spectrometer_create (taps, if any, are host memory; the
+ *               max_batch_segments field is ignored).
+ *   d_packed    n_if DEVICE pointers to the packed words; n_samples_per_if >= n_fft
+ *               and a multiple of 32/bits.
+ *   d_autos, d_cross, d_stokes  DEVICE outputs in the layouts of
+ *               spectrometer_integrate (NULL skips one).
+ * Work is queued on cuda_stream (NULL = legacy default stream); nothing is allocated
+ * and nothing synchronises the host.  The first call on a device looks up the array's
+ * device address (once per device, with that device made current); make that first
+ * call before any stream capture.  Every call reuses the same array, which keeps the
+ * previous call's contents (each call zeroes the accumulators it needs): calls whose
+ * GPU work overlaps -- on different streams or devices' shared host threads -- race on
+ * it and must be ordered by the caller.  A configuration whose accumulators, tables and
+ * one segment of slab exceed 32 MiB is rejected with POLARIS_EINVAL and a message. */
+int spectrometer_run_noalloc(const polaris_config* cfg, const void* const* d_packed, int64_t n_samples_per_if,
+                             const polaris_stokes_params* params, float* d_autos, float* d_cross, float* d_stokes,
+                             int64_t* n_segments_out, void* cuda_stream);
+
 /* Test hook: cap the bytes of device memory that later spectrometer_create
  * calls may allocate (-1 = no cap), so that allocation failure can be tested
  * without exhausting the GPU. */

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -724,5 +725,237 @@ extern "C" int spectrometer_kernel_times(polaris_spec* s, double* ms, int64_t* l
     launches[r.kind] += 1;
   }
   drop_prof(s);
+  return POLARIS_OK;
+}
+
+// =======================================================================================
+// Allocation-free one-shot variant.
+//
+// Some callers cannot allocate device memory at the point where they need a spectrum:
+// code running while a CUDA graph is being captured (cudaMalloc is not capturable),
+// real-time loops where cudaMalloc/cudaFree would synchronise the device and miss a
+// sampler deadline, and host frameworks that own all device memory through their own
+// pool and forbid other allocators.  For them spectrometer_run_noalloc computes one
+// integration without a handle: its scratch slab, accumulators, twiddle table and
+// window taps live in the file-scope array below, which every GPU that loads this
+// library holds until the process exits.
+// =======================================================================================
+#define POLARIS_NOALLOC_BYTES (32u << 20)
+static __device__ __align__(256) unsigned char g_noalloc_scratch[POLARIS_NOALLOC_BYTES];
+
+static const int kNoallocMaxDevices = 64;
+static void* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+// twiddles W_N^{b u} (b < N2, u <= N1/2) in FP64, rounded once to f32
+__global__ void k_noalloc_twiddles(float2* tw, int N2, int UPS, long long N) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)N2 * (UPS + 1);
+  if (i >= total) return;
+  const long long b = i / (UPS + 1), u = i % (UPS + 1);
+  const long long e = (b * u) % N;
+  double s, c;
+  sincospi(-2.0 * (double)e / (double)N, &s, &c);
+  tw[i] = make_float2((float)c, (float)s);
+}
+
+// periodic Hann taps 0.5 - 0.5 cos(2 pi n / N)
+__global__ void k_noalloc_hann(float* taps, long long N) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  taps[n] = (float)(0.5 - 0.5 * cospi(2.0 * (double)n / (double)N));
+}
+
+static size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* const* d_packed,
+                                        int64_t n_samples_per_if, const polaris_stokes_params* prm, float* d_autos,
+                                        float* d_cross, float* d_stokes, int64_t* n_segments_out,
+                                        void* cuda_stream) {
+  if (!cfg || !d_packed) return set_err(nullptr, POLARIS_EINVAL, "null config or input");
+  const polaris_config& c = *cfg;
+  if (c.n_if < 1 || c.n_if > kMaxIF) return set_err(nullptr, POLARIS_EINVAL, "n_if must be in [1, %d]", kMaxIF);
+  if (!(c.bits == 1 || c.bits == 2 || c.bits == 4 || c.bits == 8))
+    return set_err(nullptr, POLARIS_EINVAL, "bits must be 1, 2, 4 or 8");
+  const int64_t N = c.n_fft;
+  if (N < 16 || N > (1 << 19) || (N & (N - 1)))
+    return set_err(nullptr, POLARIS_EINVAL, "n_fft must be a power of two in [16, 524288]");
+  const int64_t spw = 32 / c.bits;
+  const int64_t hop = c.hop == 0 ? N : c.hop;
+  if (N < spw || hop < 1 || hop > N || hop % spw)
+    return set_err(nullptr, POLARIS_EINVAL, "bad n_fft/hop for %d-bit samples", c.bits);
+  if (c.window < POLARIS_WIN_RECT || c.window > POLARIS_WIN_CUSTOM || (c.window == POLARIS_WIN_CUSTOM && !c.taps))
+    return set_err(nullptr, POLARIS_EINVAL, "bad window");
+  if (n_samples_per_if < N || n_samples_per_if % spw)
+    return set_err(nullptr, POLARIS_EINVAL, "need at least one whole segment and a multiple of 32/bits samples");
+  for (int i = 0; i < c.n_if; ++i)
+    if (!d_packed[i] || (reinterpret_cast<uintptr_t>(d_packed[i]) & 3))
+      return set_err(nullptr, POLARIS_EINVAL, "input %d is NULL or not 4-byte aligned", i);
+  // pairs (same rules as spectrometer_create)
+  int pairs[2 * kMaxIF];
+  int n_pair = 0;
+  if (c.pairs) {
+    if (c.n_pair < 0 || 2 * c.n_pair > c.n_if) return set_err(nullptr, POLARIS_EINVAL, "bad n_pair");
+    n_pair = c.n_pair;
+    for (int i = 0; i < 2 * n_pair; ++i) pairs[i] = c.pairs[i];
+  } else if (c.n_if % 2 == 0) {
+    n_pair = c.n_if / 2;
+    for (int i = 0; i < n_pair; ++i) {
+      pairs[2 * i] = i;
+      pairs[2 * i + 1] = i + n_pair;
+    }
+  }
+  int used[kMaxIF] = {0};
+  for (int i = 0; i < 2 * n_pair; ++i) {
+    if (pairs[i] < 0 || pairs[i] >= c.n_if || used[pairs[i]]++)
+      return set_err(nullptr, POLARIS_EINVAL, "bad or repeated pair index");
+  }
+  int fa[kMaxIF], fb[kMaxIF], fcorr[kMaxIF];
+  int nf = 0, pending = -1;
+  for (int p = 0; p < n_pair; ++p, ++nf) {
+    fa[nf] = pairs[2 * p];
+    fb[nf] = pairs[2 * p + 1];
+    fcorr[nf] = p;
+  }
+  for (int i = 0; i < c.n_if; ++i) {
+    if (used[i]) continue;
+    if (pending < 0) pending = i;
+    else {
+      fa[nf] = pending;
+      fb[nf] = i;
+      fcorr[nf++] = -1;
+      pending = -1;
+    }
+  }
+  if (pending >= 0) {
+    fa[nf] = pending;
+    fb[nf] = -1;
+    fcorr[nf++] = -1;
+  }
+  for (int f = nf; f < kMaxIF; ++f) fa[f] = fb[f] = fcorr[f] = -1;
+  int logn = 0;
+  while ((1LL << logn) < N) ++logn;
+  const int N2 = host_plan_n2(logn), N1 = (int)(N / N2), UPS = N1 / 2, native = UPS * N2 + 1;
+  // carve the static array: accumulators | twiddles | taps | slab
+  const size_t acc_bytes = align256((size_t)nf * native * 4 * (c.accum_fp64 ? 8 : 4));
+  const size_t tw_bytes = align256((size_t)N2 * (UPS + 1) * sizeof(float2));
+  const size_t taps_bytes = c.window == POLARIS_WIN_RECT ? 0 : align256((size_t)N * 4);
+  const size_t per_seg = (size_t)nf * N * sizeof(float2);
+  const size_t fixed = acc_bytes + tw_bytes + taps_bytes;
+  if (fixed + per_seg > POLARIS_NOALLOC_BYTES)
+    return set_err(nullptr, POLARIS_EINVAL,
+                   "configuration needs %zu bytes of scratch for one segment, above the %u-byte static limit",
+                   fixed + per_seg, (unsigned)POLARIS_NOALLOC_BYTES);
+  const int batch = (int)((POLARIS_NOALLOC_BYTES - fixed) / per_seg);
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev || c.device >= kNoallocMaxDevices) {
+    cudaGetLastError();
+    return set_err(nullptr, POLARIS_EINVAL, "device ordinal out of range");
+  }
+  DeviceGuard dg(c.device);
+  // set-up, once per device: the device address of the static array
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[c.device]) {
+      void* p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess || !p) return set_err(nullptr, POLARIS_ECUDA, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      g_noalloc_ptr[c.device] = p;
+    }
+    base = static_cast<unsigned char*>(g_noalloc_ptr[c.device]);
+  }
+  void* acc = base;
+  float2* tw = reinterpret_cast<float2*>(base + acc_bytes);
+  float* taps = c.window == POLARIS_WIN_RECT ? nullptr : reinterpret_cast<float*>(base + acc_bytes + tw_bytes);
+  float2* slab = reinterpret_cast<float2*>(base + fixed);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  int num_sms = 0;
+  cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, c.device);
+  cudaError_t e = cudaMemsetAsync(acc, 0, acc_bytes, st);  // accumulators start at zero
+  if (e == cudaSuccess) {
+    const long long ntw = (long long)N2 * (UPS + 1);
+    k_noalloc_twiddles<<<(unsigned)((ntw + 255) / 256), 256, 0, st>>>(tw, N2, UPS, N);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && c.window == POLARIS_WIN_HANN) {
+    k_noalloc_hann<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(taps, N);
+    e = cudaGetLastError();
+  } else if (e == cudaSuccess && c.window == POLARIS_WIN_CUSTOM) {
+    e = cudaMemcpyAsync(taps, c.taps, (size_t)N * 4, cudaMemcpyHostToDevice, st);
+  }
+  if (e != cudaSuccess) return set_err(nullptr, POLARIS_ECUDA, "no-alloc set-up: %s", cudaGetErrorString(e));
+  const int64_t nseg = (n_samples_per_if - N) / hop + 1;
+  BatchArgs a;
+  memset(&a, 0, sizeof a);
+  for (int i = 0; i < c.n_if; ++i) {
+    a.in.src0[i] = static_cast<const uint32_t*>(d_packed[i]);
+    a.in.src1[i] = static_cast<const uint32_t*>(d_packed[i]);
+  }
+  a.in.hop_w = hop / spw;
+  a.in.n0 = 0;
+  for (int f = 0; f < kMaxIF; ++f) {
+    a.fa[f] = fa[f];
+    a.fb[f] = fb[f];
+  }
+  a.n_fpair = nf;
+  a.taps = taps;
+  a.scratch = slab;
+  a.tw = tw;
+  a.acc = acc;
+  a.fp64 = c.accum_fp64 ? 1 : 0;
+  a.bits = c.bits;
+  a.num_sms = num_sms;
+  for (int64_t s0 = 0; s0 < nseg; s0 += batch) {
+    a.seg0 = (int)s0;
+    a.nseg = (int)(nseg - s0 < batch ? nseg - s0 : batch);
+    for (int ph = 0; ph < 2 && e == cudaSuccess; ++ph) e = kPhases[logn][ph](a, st);
+    if (e != cudaSuccess) return set_err(nullptr, POLARIS_ECUDA, "no-alloc FFT-correlator: %s", cudaGetErrorString(e));
+  }
+  // readout (same kernel as spectrometer_integrate_device)
+  ReadoutArgs r;
+  memset(&r, 0, sizeof r);
+  r.acc = acc;
+  r.fp64 = a.fp64;
+  r.N1 = N1;
+  r.N2 = N2;
+  r.UPS = UPS;
+  r.nbin = (int)(N / 2 + 1);
+  r.native = native;
+  for (int f = 0; f < kMaxIF; ++f) {
+    r.fa[f] = fa[f];
+    r.fb[f] = fb[f];
+    r.fcorr[f] = fcorr[f];
+  }
+  const int feed = prm ? prm->feed : POLARIS_FEED_LINEAR;
+  if (feed != POLARIS_FEED_LINEAR && feed != POLARIS_FEED_CIRCULAR) return set_err(nullptr, POLARIS_EINVAL, "bad feed");
+  const double psi = prm ? prm->psi_m : 0.0;
+  r.feed = feed;
+  r.c2 = (float)std::cos(2.0 * psi);
+  r.s2 = (float)std::sin(2.0 * psi);
+  for (int p = 0; p < n_pair; ++p) {
+    double gar = 1, gai = 0, gbr = 1, gbi = 0;
+    if (prm && prm->gains) {
+      gar = prm->gains[4 * p + 0];
+      gai = prm->gains[4 * p + 1];
+      gbr = prm->gains[4 * p + 2];
+      gbi = prm->gains[4 * p + 3];
+    }
+    const double gaa = gar * gar + gai * gai, gbb = gbr * gbr + gbi * gbi;
+    if (gaa == 0.0 || gbb == 0.0) return set_err(nullptr, POLARIS_EINVAL, "zero gain for pair %d", p);
+    const double gr = gar * gbr + gai * gbi, gi = gai * gbr - gar * gbi, g2 = gr * gr + gi * gi;
+    r.inv_ga2[p] = (float)(1.0 / gaa);
+    r.inv_gb2[p] = (float)(1.0 / gbb);
+    r.ig_re[p] = (float)(gr / g2);
+    r.ig_im[p] = (float)(-gi / g2);
+  }
+  r.autos = d_autos;
+  r.cross = n_pair ? d_cross : nullptr;
+  r.stokes = n_pair ? d_stokes : nullptr;
+  dim3 grid((unsigned)((r.nbin + 255) / 256), (unsigned)nf);
+  k_readout<<<grid, 256, 0, st>>>(r);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return set_err(nullptr, POLARIS_ECUDA, "no-alloc readout: %s", cudaGetErrorString(e));
+  if (n_segments_out) *n_segments_out = nseg;
   return POLARIS_OK;
 }

@@ -26,7 +26,7 @@ EXPORTS = (
     "spectrometer_create", "spectrometer_feed", "spectrometer_integrate", "spectrometer_integrate_device",
     "spectrometer_n_bins", "spectrometer_n_pairs", "spectrometer_debug_unpack", "spectrometer_destroy",
     "spectrometer_last_error", "polaris_set_alloc_limit", "spectrometer_kernel_launches",
-    "spectrometer_set_profiling", "spectrometer_kernel_times",
+    "spectrometer_set_profiling", "spectrometer_kernel_times", "spectrometer_run_noalloc",
 )
 
 
@@ -88,6 +88,10 @@ def load(path: str = LIB_PATH):
             lib.spectrometer_set_profiling.restype = ci
             lib.spectrometer_kernel_times.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64), ci]
             lib.spectrometer_kernel_times.restype = ci
+            lib.spectrometer_run_noalloc.argtypes = [ctypes.POINTER(polaris_config), ctypes.POINTER(vp), i64,
+                                                     ctypes.POINTER(polaris_stokes_params), vp, vp, vp,
+                                                     ctypes.POINTER(i64), vp]
+            lib.spectrometer_run_noalloc.restype = ci
             lib.polaris_set_alloc_limit.argtypes = [i64]
             lib.polaris_set_alloc_limit.restype = None
             _lib = lib
@@ -238,3 +242,41 @@ class Spectrometer:
         out = np.empty(max(n, 1), np.float32)
         self._check(load().spectrometer_debug_unpack(self._h, w.ctypes.data, int(n), out.ctypes.data))
         return out[:n]
+
+
+def run_noalloc(packed, n_samples: int, bits: int, n_fft: int, autos, cross, stokes, hop: int = 0, window="rect",
+                pairs=None, accum_fp64: bool = False, device: int = 0, feed: int = FEED_LINEAR, psi: float = 0.0,
+                gains=None, stream=None) -> int:
+    """spectrometer_run_noalloc: one integration of device-resident packed streams into
+    device output tensors, using only the library's static device array (no allocation
+    by the library).  For callers that cannot allocate device memory at this point, e.g.
+    while a CUDA graph is captured or inside a real-time loop.  Returns the segment count."""
+    lib = load()
+    cfg = polaris_config()
+    cfg.n_if, cfg.bits, cfg.n_fft, cfg.hop = len(packed), bits, n_fft, hop
+    keep = []
+    if isinstance(window, str):
+        cfg.window = {"rect": WIN_RECT, "hann": WIN_HANN}[window]
+    else:
+        t = np.ascontiguousarray(window, dtype=np.float32)
+        keep.append(t)
+        cfg.window = WIN_CUSTOM
+        cfg.taps = t.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    if pairs is not None:
+        pr = np.ascontiguousarray(np.array(pairs, dtype=np.int32).reshape(-1))
+        keep.append(pr)
+        cfg.n_pair = len(pr) // 2
+        cfg.pairs = pr.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+    cfg.accum_fp64 = int(bool(accum_fp64))
+    cfg.device = device
+    arr = (ctypes.c_void_p * len(packed))(*[_ptr(p) for p in packed])
+    p, g = Spectrometer._params(feed, psi, gains)
+    nseg = ctypes.c_int64(0)
+    rc = lib.spectrometer_run_noalloc(ctypes.byref(cfg), arr, int(n_samples), ctypes.byref(p),
+                                      None if autos is None else _ptr(autos), None if cross is None else _ptr(cross),
+                                      None if stokes is None else _ptr(stokes), ctypes.byref(nseg),
+                                      _stream_ptr(stream))
+    del g, keep
+    if rc != OK:
+        raise PolarisError(rc, lib.spectrometer_last_error(None).decode())
+    return int(nseg.value)
