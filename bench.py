@@ -255,7 +255,7 @@ def run_ours(args, rank, world, local_rank, dist):
     cross = torch.empty((N_PAIR, NBIN, 2), dtype=torch.float32, device=dev)
     stokes = torch.empty((N_PAIR, 4, NBIN), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    sp = polaris.Spectrometer(N_IF, BITS, N_FFT, device=local_rank)
+    sp = polaris.Spectrometer(N_IF, BITS, N_FFT, device=local_rank, max_batch_segments=args.batch_segments)
 
     def step(i):
         sec = ring[i % ring_n]
@@ -397,6 +397,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--cpu-segs", type=int, default=61)
     ap.add_argument("--cpu-repeats", type=int, default=2)
+    ap.add_argument("--batch-segments", type=int, default=0,
+                    help="segments per kernel pass (0: the library's default, sized to keep the slab in L2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -76,8 +76,8 @@ typedef struct polaris_spec polaris_spec; /* opaque, library-owned */
  *               FP32); 0: FP32.
  *   device      CUDA device ordinal.
  *   max_batch_segments  segments processed per kernel pass (bounds the device
- *               scratch: max_batch_segments * n_fft * 8 bytes per pair);
- *               0 selects a default that keeps the scratch inside L2. */
+ *               scratch: 2 * max_batch_segments * n_fft * 8 bytes per pair);
+ *               0 selects the default (passes of at least 64 segments). */
 typedef struct {
   int n_if;
   int bits;

@@ -40,8 +40,12 @@ def _newest_header() -> float:
     return max((os.path.getmtime(h) for h in hs), default=0.0)
 
 
-def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
-    """Compile and link libpolaris.so; return its path."""
+def build(force: bool = False, jobs: int | None = None, verbose: bool = False, out_dir: str | None = None,
+          defines: tuple = ()) -> str:
+    """Compile and link libpolaris.so; return its path.  out_dir/defines build a variant
+    (objects and library in out_dir, extra -D flags) without touching the default build."""
+    BUILD = os.path.join(out_dir, "_build") if out_dir else globals()["BUILD"]
+    LIB = os.path.join(out_dir, "libpolaris.so") if out_dir else globals()["LIB"]
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
@@ -56,7 +60,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
 
     def comp(so):
         s, o = so
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", s, "-o", o + ".tmp"]
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *[f"-D{d}" for d in defines], "-c", s, "-o", o + ".tmp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {os.path.basename(s)}:\n{r.stderr[-4000:]}")

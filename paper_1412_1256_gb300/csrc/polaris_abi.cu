@@ -175,6 +175,11 @@ struct polaris_spec {
   float* d_out_cross = nullptr;
   float* d_out_stokes = nullptr;
   cudaEvent_t ev_h2d = nullptr;
+  // two internal streams: phase 1 of batch b+1 runs beside phase 2 of batch b; the
+  // slab is split into two halves used by alternate batches
+  cudaStream_t st_p1 = nullptr, st_p2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_p1[2] = {nullptr, nullptr}, ev_p2[2] = {nullptr, nullptr};
+  size_t slab_half = 0;  // float2 elements per slab half
   int64_t seg_acc = 0;  // segments accumulated in the open integration
   int64_t launches = 0; // kernels launched by this handle (all kinds)
   bool profiling = false;
@@ -268,6 +273,10 @@ static cudaError_t counted_launch(polaris_spec* s, int kind, cudaStream_t st, F&
 }
 
 static void free_all(polaris_spec* s) {
+  if (s->st_p1) cudaStreamDestroy(s->st_p1);
+  if (s->st_p2) cudaStreamDestroy(s->st_p2);
+  for (cudaEvent_t e : {s->ev_fork, s->ev_join, s->ev_p1[0], s->ev_p1[1], s->ev_p2[0], s->ev_p2[1]})
+    if (e) cudaEventDestroy(e);
   drop_prof(s);
   for (cudaEvent_t e : s->spare) cudaEventDestroy(e);
   s->spare.clear();
@@ -383,18 +392,22 @@ extern "C" int spectrometer_create(const polaris_config* cfg, polaris_spec** out
 
   DeviceGuard dg(c.device);
   cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, c.device);
-  // batch size: keep the per-batch scratch (segments * FFT pairs * N * 8 bytes) near 48 MB
+  // batch size: segments per kernel pass.  Each pass pays a ramp and a tail on every SM, so
+  // the default takes large passes (each slab half up to ~256 MB, at least 64 segments);
+  // the slab then streams through HBM, which has bandwidth to spare for this path.
   if (c.max_batch_segments > 0) s->max_batch = c.max_batch_segments;
   else {
     const int64_t per_seg = (int64_t)nf * N * 8;
-    int64_t mb = (48LL << 20) / per_seg;
-    s->max_batch = (int)(mb < 1 ? 1 : (mb > 4096 ? 4096 : mb));
+    int64_t mb = (256LL << 20) / per_seg;
+    if (mb < 64) mb = 64;
+    s->max_batch = (int)(mb > 4096 ? 4096 : mb);
   }
+  s->slab_half = (size_t)s->max_batch * nf * N;
   s->carry_words_cap = N / spw;               // carried samples < N
   s->stage_words_cap = 2 * N / spw;           // staging < carry + N samples
   const size_t acc_bytes = (size_t)nf * s->native * 4 * (s->accum_fp64 ? 8 : 4);
   const size_t bytes_tw = (size_t)s->N2 * (s->UPS + 1) * sizeof(float2);
-  const size_t bytes_scratch = (size_t)s->max_batch * nf * N * sizeof(float2);
+  const size_t bytes_scratch = 2 * (size_t)s->max_batch * nf * N * sizeof(float2);
   const size_t bytes_carry = (size_t)c.n_if * s->carry_words_cap * 4;
   const size_t bytes_stage = (size_t)c.n_if * s->stage_words_cap * 4;
   const size_t bytes_out = (size_t)s->nbin * 4 * (c.n_if + 2 * n_pair + 4 * n_pair);
@@ -440,6 +453,10 @@ extern "C" int spectrometer_create(const polaris_config* cfg, polaris_spec** out
   }
   if (e == cudaSuccess) e = cudaMemset(s->d_acc, 0, acc_bytes);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_h2d, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st_p1, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st_p2, cudaStreamNonBlocking);
+  for (cudaEvent_t* ev : {&s->ev_fork, &s->ev_join, &s->ev_p1[0], &s->ev_p1[1], &s->ev_p2[0], &s->ev_p2[1]})
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_all(s);
@@ -548,14 +565,30 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
   a.fp64 = s->accum_fp64;
   a.bits = s->bits;
   a.num_sms = s->num_sms;
-  for (int64_t s0 = 0; s0 < nseg; s0 += s->max_batch) {
-    a.seg0 = (int)s0;
-    a.nseg = (int)(nseg - s0 < s->max_batch ? nseg - s0 : s->max_batch);
-    for (int ph = 0; ph < 2; ++ph) {
-      const phase_fn fn = kPhases[s->logn][ph];
-      cudaError_t e = counted_launch(s, ph, st, [&]() { return fn(a, st); });
-      if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "FFT-correlator launch: %s", cudaGetErrorString(e));
+  if (nseg > 0) {
+    // fork: both internal streams start after everything queued so far on the caller's stream
+    CUDA_OR_FAIL(s, cudaEventRecord(s->ev_fork, st));
+    CUDA_OR_FAIL(s, cudaStreamWaitEvent(s->st_p1, s->ev_fork, 0));
+    CUDA_OR_FAIL(s, cudaStreamWaitEvent(s->st_p2, s->ev_fork, 0));
+    int b = 0;
+    for (int64_t s0 = 0; s0 < nseg; s0 += s->max_batch, ++b) {
+      a.seg0 = (int)s0;
+      a.nseg = (int)(nseg - s0 < s->max_batch ? nseg - s0 : s->max_batch);
+      a.scratch = s->d_scratch + (size_t)(b & 1) * s->slab_half;
+      // phase 1 of batch b may overwrite its slab half once phase 2 of batch b-2 has read it
+      if (b >= 2) CUDA_OR_FAIL(s, cudaStreamWaitEvent(s->st_p1, s->ev_p2[b & 1], 0));
+      const phase_fn f1 = kPhases[s->logn][0], f2 = kPhases[s->logn][1];
+      cudaError_t e = counted_launch(s, 0, s->st_p1, [&]() { return f1(a, s->st_p1); });
+      if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "phase-1 launch: %s", cudaGetErrorString(e));
+      CUDA_OR_FAIL(s, cudaEventRecord(s->ev_p1[b & 1], s->st_p1));
+      CUDA_OR_FAIL(s, cudaStreamWaitEvent(s->st_p2, s->ev_p1[b & 1], 0));
+      e = counted_launch(s, 1, s->st_p2, [&]() { return f2(a, s->st_p2); });
+      if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "phase-2 launch: %s", cudaGetErrorString(e));
+      CUDA_OR_FAIL(s, cudaEventRecord(s->ev_p2[b & 1], s->st_p2));
     }
+    // join: phase 2 of the last batch follows every phase 1, so waiting on st_p2 suffices
+    CUDA_OR_FAIL(s, cudaEventRecord(s->ev_join, s->st_p2));
+    CUDA_OR_FAIL(s, cudaStreamWaitEvent(st, s->ev_join, 0));
   }
   // carry the samples after the last whole segment: stream positions [nseg*hop, total)
   const int64_t keep0 = nseg * hop, keep = total - keep0;

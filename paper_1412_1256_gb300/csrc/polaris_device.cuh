@@ -183,6 +183,48 @@ constexpr int plan_log_n2(int logn) {
   // 4:2 5:3 6:3 7:4 8:4 9:5 10:5 11:6 12:6 13:7 14:7 15:8 16:8 17:9 18:9 19:9
   return logn >= 17 ? 9 : (logn + 1) / 2;
 }
+// ----------------------------------------------------------------------------------------
+// shared-memory layouts of the warp-local transposes.  The strides below were chosen by an
+// offline simulation of the bank conflicts of each transpose's write and read patterns
+// (8-byte elements; a warp access costs max over the 16 bank pairs of the distinct elements
+// that fall on it): they give the minimum of 2 wavefronts per access for the phase-1
+// layouts and for phase 2 at Q2 = 16 and Q2 = 2 with P = 4, and at most 4 otherwise.
+//   phase 1, element (q, p, cw) at q * LDQ1 + p * LDP1 + cw
+//   phase 2, element (unit, e, p, q) at (unit * 2 + e) * LDE2 + p * LDQ2 + q
+// ----------------------------------------------------------------------------------------
+namespace bank {
+struct Ld2 {
+  int a, b;
+};
+constexpr Ld2 p1_layout(int P, int Q1) {
+  return (P == 32 && Q1 == 2)    ? Ld2{16, 512}
+         : (P == 32 && Q1 == 4)  ? Ld2{9, 292}
+         : (P == 32 && Q1 == 8)  ? Ld2{5, 162}
+         : (P == 32 && Q1 == 16) ? Ld2{3, 97}
+         : (P == 32 && Q1 == 32) ? Ld2{1, 33}
+                                 : Ld2{32 / Q1, P * (32 / Q1)};  // Q1 = 1: no transpose
+}
+constexpr Ld2 p2_layout(int P, int Q2) {
+  return (P == 32 && Q2 == 16)  ? Ld2{17, 544}
+         : (P == 32 && Q2 == 8) ? Ld2{9, 288}
+         : (P == 32 && Q2 == 4) ? Ld2{5, 161}
+         : (P == 32 && Q2 == 2) ? Ld2{2, 65}
+         : (P == 32 && Q2 == 1) ? Ld2{1, 33}
+         : (P == 16 && Q2 == 2) ? Ld2{2, 33}
+         : (P == 16 && Q2 == 1) ? Ld2{1, 17}
+         : (P == 8 && Q2 == 2)  ? Ld2{2, 17}
+         : (P == 8 && Q2 == 1)  ? Ld2{1, 9}
+         : (P == 4 && Q2 == 2)  ? Ld2{3, 13}
+                                : Ld2{1, 5};  // P = 4, Q2 = 1
+}
+}  // namespace bank
+
+constexpr int pow2_at_least(int v, int lo) {
+  int r = lo;
+  while (r < v) r *= 2;
+  return r;
+}
+
 template <int LOGN>
 struct Plan {
   static constexpr int N = 1 << LOGN;
@@ -191,25 +233,52 @@ struct Plan {
   static constexpr int N1 = N / N2;
   static constexpr int Q1 = N1 / P;
   static constexpr int Q2 = N2 / P;
-  static constexpr int T1 = 512;  // phase-1 threads
-  static constexpr int T2 = 256;  // phase-2 threads
-  static constexpr int W = T1 * P / N1;        // phase-1 columns per tile
-  static constexpr int U = T2 * P / (2 * N2);  // phase-2 units per tile
-  static constexpr int UPS = N1 / 2;           // units per pair-segment
-  static constexpr int SLOTS = U > UPS ? U / UPS : 1;  // segments in flight per phase-2 tile
-  static constexpr int NUB = U > UPS ? 1 : UPS / U;    // unit blocks per pair-segment
-  static constexpr int PP = P / (2 * Q2);              // p-values per thread after the joint transpose
-  static constexpr int NACC = P / 2;                   // accumulator slots (bins) per phase-2 thread
+  static constexpr int UPS = N1 / 2;                   // units (column + mirror) per pair-segment
+  static constexpr int NACC = P / 2;                   // accumulator bins per phase-2 lane
   static constexpr int NATIVE = UPS * N2 + 1;          // native accumulator bins per FFT pair (= N/2 + 1)
-  static constexpr int S1_LD = W + 1;                  // padded row of the phase-1 transpose buffer
-  static constexpr int S2_LD = 2 * U + 1;              // padded row of the phase-2 transpose buffer
-  static constexpr size_t SMEM1 = sizeof(float2) * (size_t)Q1 * P * S1_LD;
-  static constexpr size_t SMEM2 = sizeof(float2) * ((size_t)Q2 * P * S2_LD + (size_t)SLOTS * 2 * N2);
+  static constexpr int THREADS = 256;                  // threads per CTA of both phase kernels
+  static constexpr int WARPS = THREADS / 32;
+
+  // phase 1: a warp owns CW columns; lane = q1 * CW + cw holds rows q1 + Q1 t
+  static constexpr int CW = 32 / Q1;
+  static constexpr int PQ = P / Q1;
+  static constexpr bank::Ld2 L1 = bank::p1_layout(P, Q1);
+  static constexpr int LDP1 = L1.a, LDQ1 = L1.b;
+  static constexpr int REGION1 = Q1 > 1 ? Q1 * LDQ1 : 0;  // float2 per warp
+  static constexpr int TW1 = ((2 * P + 15) / 16) * 16;      // tensor-memory columns per lane (W_N1 twiddles)
+  static constexpr int TCOLS1 = pow2_at_least((WARPS / 4) * TW1, 32);
+  // CTA tiles of WARPS * CW columns inside one segment: the CTA stages the tile's packed
+  // words (both IFs) in shared memory; otherwise (small N) every lane loads its own words
+  static constexpr int TILE1 = WARPS * CW;
+  static constexpr bool STAGED1 = (N2 % TILE1 == 0) && (TILE1 % 32 == 0);
+  template <int BITS>
+  static constexpr int stage_row() { return 2 * (TILE1 * BITS / 32) + 1; }  // both IFs + 1 pad word
+  template <int BITS>
+  static constexpr int stage_words() { return STAGED1 ? 2 * N1 * stage_row<BITS>() : 0; }  // 2 buffers
+  template <int BITS>
+  static constexpr size_t smem1() {
+    return sizeof(float2) * (size_t)WARPS * REGION1 + 4 * (size_t)stage_words<BITS>() + 16;
+  }
+
+  // phase 2: a warp owns UPW units; lane = (uw * 2 + e) * Q2 + q2 holds rows q2 + Q2 t
+  static constexpr int UPW = 16 / Q2;
+  static constexpr int PP = P / (2 * Q2);                  // p-values per lane after the joint transpose
+  static constexpr int SL = UPW > UPS ? UPW / UPS : 1;     // segments in flight per warp (small N)
+  static constexpr int UGW = UPW > UPS ? 1 : UPS / UPW;    // unit groups per pair-segment
+  static constexpr bank::Ld2 L2 = bank::p2_layout(P, Q2);
+  static constexpr int LDQ2 = L2.a, LDE2 = L2.b;
+  static constexpr int REGION2 = (2 * UPW * LDE2 > 2 * UPW * N2) ? 2 * UPW * LDE2 : 2 * UPW * N2;
+  static constexpr int TWT = N2 + N2 / 32 + 1;             // skewed W_N2 table (index k + k/32)
+  static constexpr int TACC = ((2 * P + 15) / 16) * 16;    // tensor-memory columns per lane: accumulators
+  static constexpr int TTW = ((2 * P + 15) / 16) * 16;     // and the lane's column twiddles W_N^{b u}
+  static constexpr int TCOLS2 = pow2_at_least((WARPS / 4) * (TACC + TTW), 32);
+  static constexpr size_t SMEM2 = sizeof(float2) * ((size_t)WARPS * REGION2 + TWT) + 16;
+
   static_assert(N1 * N2 == N, "plan");
-  static_assert(Q1 >= 1 && Q1 <= P && Q2 >= 1 && 2 * Q2 <= P, "plan bounds");
-  static_assert(W >= 1 && U >= 1 && T1 % W == 0 && T2 % (2 * U) == 0, "tiles");
-  static_assert(UPS % U == 0 || U % UPS == 0, "units");
+  static_assert(Q1 >= 1 && Q1 <= 32 && P % Q1 == 0 && Q2 >= 1 && 2 * Q2 <= P && 16 % Q2 == 0, "plan bounds");
   static_assert(N1 <= 1024 && N2 <= 1024, "constant twiddle table covers L <= 1024");
+  static_assert(UPS % UPW == 0 || UPW % UPS == 0, "units per warp");
+  static_assert(TCOLS1 <= 256 && TCOLS2 <= 256, "tensor memory per CTA");
 };
 
 }  // namespace polaris

@@ -3,8 +3,8 @@
 //   k_phase1  data translation (codes -> levels, Fig. 2 caption), window (Sec. 3.1),
 //             first half of the segment FFT: for every column b of n = N2 a + b a DFT of
 //             length N1 over the rows a, done in registers (P points per thread) with one
-//             transpose through shared memory.  Writes the N complex partial transforms of
-//             each pair-segment to an L2-resident scratch slab, row b contiguous in c.
+//             warp-local transpose through shared memory.  Writes the N complex partial
+//             transforms of each pair-segment to a scratch slab [pair-segment][c][b].
 //
 //   k_phase2  second half of the FFT and the correlator (Fig. 1 caption: XX*, YY*, XY*;
 //             Table 1; accumulation over the integration): for every output column c the
@@ -75,6 +75,55 @@ __device__ __forceinline__ const uint32_t* seg_ptr(const SegSrc& in, int ifx, in
   return s < in.n0 ? in.src0[ifx] + (long long)s * in.hop_w : in.src1[ifx] + (long long)(s - in.n0) * in.hop_w;
 }
 
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// ------------------------------------------------------------------------------------------
+// tensor memory (TMEM) as per-thread storage: warp w reaches lanes 32 (w % 4) .. +31; a
+// thread owns one lane and a range of 32-bit columns.  All tcgen05 calls below are
+// warp-wide (.sync.aligned) and are made by converged warps only.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {  // one warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {  // the allocating warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+// 16 consecutive columns of this thread's lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&r)[16]) {
+  uint32_t u[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]),
+        "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) r[i] = __uint_as_float(u[i]);
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+          taddr),
+      "r"(__float_as_uint(r[0])), "r"(__float_as_uint(r[1])), "r"(__float_as_uint(r[2])), "r"(__float_as_uint(r[3])),
+      "r"(__float_as_uint(r[4])), "r"(__float_as_uint(r[5])), "r"(__float_as_uint(r[6])), "r"(__float_as_uint(r[7])),
+      "r"(__float_as_uint(r[8])), "r"(__float_as_uint(r[9])), "r"(__float_as_uint(r[10])),
+      "r"(__float_as_uint(r[11])), "r"(__float_as_uint(r[12])), "r"(__float_as_uint(r[13])),
+      "r"(__float_as_uint(r[14])), "r"(__float_as_uint(r[15]))
+      : "memory");
+}
+
 // ------------------------------------------------------------------------------------------
 // phase 1
 // ------------------------------------------------------------------------------------------
@@ -111,63 +160,6 @@ __device__ __forceinline__ void p1_load(const BatchArgs& a, int g, int b, int q1
   });
 }
 
-template <int LOGN, int BITS>
-__global__ void __launch_bounds__(Plan<LOGN>::T1, 1) k_phase1(BatchArgs a) {
-  using PL = Plan<LOGN>;
-  constexpr int P = PL::P, N1 = PL::N1, N2 = PL::N2, Q1 = PL::Q1, W = PL::W, LD = PL::S1_LD;
-  extern __shared__ float2 sm1[];
-  const int tid = threadIdx.x;
-  const long long total_cols = (long long)a.nseg * a.n_fpair * N2;
-  {
-    const int q1 = tid / W, w = tid % W;
-    const long long gc = (long long)blockIdx.x * W + w;
-    float2 v[P];
-    if (gc < total_cols) {
-      p1_load<LOGN, BITS>(a, (int)(gc / N2), (int)(gc % N2), q1, v);
-    } else {
-      sfor<0, P>([&](auto t_) { v[decltype(t_)::value] = make_float2(0.f, 0.f); });
-    }
-    dit<P>(v);
-    if constexpr (Q1 > 1) {
-      sfor<1, P>([&](auto p_) {
-        constexpr int p = decltype(p_)::value;
-        v[p] = cmul(v[p], tw_small<N1>(q1 * p));
-      });
-    }
-    sfor<0, P>([&](auto p_) {
-      constexpr int p = decltype(p_)::value;
-      sm1[(q1 * P + p) * LD + w] = v[p];
-    });
-  }
-  __syncthreads();
-  {
-    constexpr int CPT = P / Q1;  // columns per thread in the second step
-    const int p = tid % P, wg = tid / P;
-    sfor<0, CPT>([&](auto i_) {
-      constexpr int i = decltype(i_)::value;
-      const int w = wg * CPT + i;
-      const long long gc = (long long)blockIdx.x * W + w;
-      float2 u[Q1];
-      sfor<0, Q1>([&](auto q_) {
-        constexpr int q = decltype(q_)::value;
-        u[ct::bitrev(q, Q1)] = sm1[(q * P + p) * LD + w];
-      });
-      dit<Q1>(u);
-      if (gc < total_cols) {
-        const long long g = gc / N2, b = gc % N2;
-        float2* dst = a.scratch + ((size_t)g * N2 + b) * N1 + p;
-        sfor<0, Q1>([&](auto m_) {
-          constexpr int m = decltype(m_)::value;
-          dst[m * P] = u[m];
-        });
-      }
-    });
-  }
-}
-
-// ------------------------------------------------------------------------------------------
-// phase 2
-// ------------------------------------------------------------------------------------------
 __device__ __forceinline__ void corr_acc(float (&acc)[4], float2 U, float2 V) {
   // S = 2X, D = 2iY;  |S|^2, |D|^2, Re/Im of i S conj(D) (= 4 X conj(Y))
   const float sx = U.x + V.x, sy = U.y + V.y, dx = U.x - V.x, dy = U.y - V.y;
@@ -177,201 +169,477 @@ __device__ __forceinline__ void corr_acc(float (&acc)[4], float2 U, float2 V) {
   acc[3] = fmaf(sx, dx, fmaf(sy, dy, acc[3]));
 }
 
-template <int LOGN>
-__global__ void __launch_bounds__(Plan<LOGN>::T2, 1) k_phase2(BatchArgs a, int seg_per_tile, int n_chunks) {
-  using PL = Plan<LOGN>;
-  constexpr int P = PL::P, N1 = PL::N1, N2 = PL::N2, Q2 = PL::Q2, U = PL::U, UPS = PL::UPS;
-  constexpr int SLOTS = PL::SLOTS, NUB = PL::NUB, PP = PL::PP, NACC = PL::NACC, LD = PL::S2_LD;
-  extern __shared__ float2 sm2[];
-  float2* sp = sm2 + Q2 * P * LD;  // mirror area for the special unit: [SLOTS][2][N2]
-  const int tid = threadIdx.x;
 
-  const int chunk = blockIdx.x % n_chunks;
-  const int fub = blockIdx.x / n_chunks;
-  const int ub = fub % NUB, f = fub / NUB;
-  const int s_begin = chunk * seg_per_tile;
-  const int s_end = min(a.nseg, s_begin + seg_per_tile);
 
-  // step-1 mapping: lanes over the tile's 2U columns, q2 over warps
-  const int col = tid % (2 * U), q2 = tid / (2 * U);
-  const int e1 = col / U, i1 = col % U;
-  const int so1 = (U > UPS) ? i1 / UPS : 0;
-  const int u1 = (U > UPS) ? i1 % UPS : ub * U + i1;
-  const int c1 = (u1 == 0) ? (e1 ? N1 / 2 : 0) : (e1 ? N1 - u1 : u1);
-  const int tu1 = (u1 == 0 && e1) ? N1 / 2 : u1;
-  const bool cj1 = e1 && u1 != 0;
-  // step-2 mapping: one unit per 2 Q2 threads, p-values j2 * PP + r
-  const int j2 = tid % (2 * Q2), i2 = tid / (2 * Q2);
-  const int so2 = (U > UPS) ? i2 / UPS : 0;
-  const int u2 = (U > UPS) ? i2 % UPS : ub * U + i2;
-  const bool special2 = (u2 == 0);
-  const bool tile_special = (U > UPS) || (ub == 0);
-
-  float acc[NACC][4];
-  float extra[4] = {0.f, 0.f, 0.f, 0.f};
-  sfor<0, NACC>([&](auto k_) {
-    constexpr int k = decltype(k_)::value;
-    acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0.f;
-  });
-
-  const int n_iter = (s_end - s_begin + SLOTS - 1) / SLOTS;
-  for (int it = 0; it < n_iter; ++it) {
-    {
-      const int s = s_begin + it * SLOTS + so1;
-      const bool act = s < s_end;
-      const float2* src = a.scratch + ((size_t)(act ? s : 0) * a.n_fpair + f) * N2 * N1 + c1;
-      const float2* twp = a.tw + tu1;
-      float2 v[P];
-      sfor<0, P>([&](auto t_) {
-        constexpr int t = decltype(t_)::value;
-        const int b = q2 + Q2 * t;
-        const float2 z = act ? __ldcg(src + (size_t)b * N1) : make_float2(0.f, 0.f);
-        const float2 w = __ldg(twp + b * (UPS + 1));
-        v[ct::bitrev(t, P)] = cj1 ? cmulc(z, w) : cmul(z, w);
-      });
-      dit<P>(v);
-      if constexpr (Q2 > 1) {
-        sfor<1, P>([&](auto p_) {
-          constexpr int p = decltype(p_)::value;
-          v[p] = cmul(v[p], tw_small<N2>(q2 * p));
-        });
-      }
-      __syncthreads();  // previous iteration's readers are done with sm2
-      sfor<0, P>([&](auto p_) {
-        constexpr int p = decltype(p_)::value;
-        sm2[(q2 * P + p) * LD + col] = v[p];
-      });
-    }
-    __syncthreads();
-    // step 2: DFT-Q2 for both members (e) of the unit and PP p-values
-    float2 wv[2 * PP * Q2];
-    sfor<0, 2>([&](auto e_) {
-      constexpr int e = decltype(e_)::value;
-      sfor<0, PP>([&](auto r_) {
-        constexpr int r = decltype(r_)::value;
-        const int p = j2 * PP + r;
-        sfor<0, Q2>([&](auto q_) {
-          constexpr int q = decltype(q_)::value;
-          wv[(e * PP + r) * Q2 + ct::bitrev(q, Q2)] = sm2[(q * P + p) * LD + e * U + i2];
-        });
-        dit<Q2, (e * PP + r) * Q2, 1>(wv);
-      });
-    });
-    const int s2 = s_begin + it * SLOTS + so2;
-    const bool act2 = s2 < s_end;
-    if (tile_special) {  // uniform per tile
-      if (special2) {
-        sfor<0, 2>([&](auto e_) {
-          constexpr int e = decltype(e_)::value;
-          sfor<0, PP>([&](auto r_) {
-            constexpr int r = decltype(r_)::value;
-            sfor<0, Q2>([&](auto m_) {
-              constexpr int m = decltype(m_)::value;
-              const int d = j2 * PP + r + P * m;
-              sp[(so2 * 2 + e) * N2 + d] = wv[(e * PP + r) * Q2 + m];
-            });
-          });
-        });
-      }
-      __syncthreads();
-    }
-    if (act2) {
-      if (!special2) {
-        sfor<0, PP>([&](auto r_) {
-          constexpr int r = decltype(r_)::value;
-          sfor<0, Q2>([&](auto m_) {
-            constexpr int m = decltype(m_)::value;
-            corr_acc(acc[r * Q2 + m], wv[r * Q2 + m], wv[(PP + r) * Q2 + m]);
-          });
-        });
-      } else {
-        const float2* s0 = sp + (so2 * 2 + 0) * N2;  // column 0
-        const float2* sh = sp + (so2 * 2 + 1) * N2;  // column N1/2
-        sfor<0, PP>([&](auto r_) {
-          constexpr int r = decltype(r_)::value;
-          sfor<0, Q2>([&](auto m_) {
-            constexpr int m = decltype(m_)::value;
-            const int d = j2 * PP + r + P * m;
-            float2 Uv, Vv;
-            if (d <= N2 / 2) {  // column 0: bins N1 d, mirror N1 (N2 - d)
-              Uv = s0[d];
-              const float2 t = s0[(N2 - d) & (N2 - 1)];
-              Vv = make_float2(t.x, -t.y);
-            } else {  // column N1/2 at dh = d - N2/2 - 1: bins N1/2 + N1 dh, mirror dh' = N2 - 1 - dh
-              const int dh = d - N2 / 2 - 1;
-              Uv = sh[dh];
-              const float2 t = sh[N2 - 1 - dh];
-              Vv = make_float2(t.x, -t.y);
-            }
-            corr_acc(acc[r * Q2 + m], Uv, Vv);
-          });
-        });
-        if (j2 == 0) {  // the one extra bin: column N1/2 at dh = N2/2 - 1
-          const float2 t = sh[N2 / 2];
-          corr_acc(extra, sh[N2 / 2 - 1], make_float2(t.x, -t.y));
-        }
-      }
-    }
-  }
-
-  // flush: one atomic add per bin into the integration accumulators (native order)
-  const bool had_work = (s_begin + so2) < s_end;
-  if (!had_work) return;
-  const size_t base = (size_t)f * PL::NATIVE;
-  if (!a.fp64) {
-    float4* accp = reinterpret_cast<float4*>(a.acc) + base;
-    sfor<0, PP>([&](auto r_) {
-      constexpr int r = decltype(r_)::value;
-      sfor<0, Q2>([&](auto m_) {
-        constexpr int m = decltype(m_)::value;
-        const int d = j2 * PP + r + P * m;
-        const float* q = acc[r * Q2 + m];
-        atomicAdd(accp + (size_t)u2 * N2 + d, make_float4(q[0], q[1], q[2], q[3]));
-      });
-    });
-    if (special2 && j2 == 0) atomicAdd(accp + (size_t)UPS * N2, make_float4(extra[0], extra[1], extra[2], extra[3]));
-  } else {
-    double* accp = reinterpret_cast<double*>(a.acc) + 4 * base;
-    sfor<0, PP>([&](auto r_) {
-      constexpr int r = decltype(r_)::value;
-      sfor<0, Q2>([&](auto m_) {
-        constexpr int m = decltype(m_)::value;
-        const int d = j2 * PP + r + P * m;
-        const float* q = acc[r * Q2 + m];
-        double* o = accp + 4 * ((size_t)u2 * N2 + d);
-        atomicAdd(o + 0, (double)q[0]);
-        atomicAdd(o + 1, (double)q[1]);
-        atomicAdd(o + 2, (double)q[2]);
-        atomicAdd(o + 3, (double)q[3]);
-      });
-    });
-    if (special2 && j2 == 0) {
-      double* o = accp + 4 * (size_t)UPS * N2;
-      atomicAdd(o + 0, (double)extra[0]);
-      atomicAdd(o + 1, (double)extra[1]);
-      atomicAdd(o + 2, (double)extra[2]);
-      atomicAdd(o + 3, (double)extra[3]);
-    }
+// ------------------------------------------------------------------------------------------
+// warp-owned work: no CTA-wide barrier inside the loops.  Each warp allocates nothing; the
+// CTA takes its tensor memory once (warp 0) and gives it back at the end.
+// ------------------------------------------------------------------------------------------
+template <int TCOLS>
+__device__ __forceinline__ uint32_t cta_tmem_begin(uint32_t* slot, int warp) {
+  if (warp == 0) tmem_alloc(slot, TCOLS);
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  return *slot;
+}
+template <int TCOLS>
+__device__ __forceinline__ void cta_tmem_end(uint32_t tbase, int warp) {
+  tmem_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tmem_fence_after();
+    tmem_dealloc(tbase, TCOLS);
   }
 }
 
 // ------------------------------------------------------------------------------------------
-// host-side launcher for one batch of segments (instantiated once per N)
+// phase 1: a warp owns CW = 32/Q1 adjacent columns of the slab; lane (q1, cw) loads rows
+// q1 + Q1 t of column cw, runs the P-point DFT in registers, twiddles by W_N1^{q1 p} (held in
+// its tensor-memory lane), transposes through the warp's shared-memory region and finishes
+// the N1-point DFT with Q1-point register DFTs.  Output slab layout: [pair-segment][c][b].
 // ------------------------------------------------------------------------------------------
+template <int LOGN, int BITS>
+__global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase1(BatchArgs a) {
+  using PL = Plan<LOGN>;
+  constexpr int P = PL::P, N1 = PL::N1, N2 = PL::N2, Q1 = PL::Q1, CW = PL::CW, PQ = PL::PQ;
+  constexpr int LDP = PL::LDP1, LDQ = PL::LDQ1;
+  constexpr bool STAGED = PL::STAGED1;
+  constexpr int TILE = PL::TILE1, WPR = STAGED ? TILE * BITS / 32 : 1;  // words per row of a tile
+  extern __shared__ float2 sm1[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q1 = lane / CW, cw = lane % CW;
+  float2* region = sm1 + warp * PL::REGION1;
+  uint32_t* stage = reinterpret_cast<uint32_t*>(sm1 + PL::WARPS * PL::REGION1);  // [row][IF pair][WPR]
+  uint32_t* tslot = stage + PL::template stage_words<BITS>();
+
+  uint32_t tbase = 0, t_tw = 0;
+  if constexpr (Q1 > 1) {
+    tbase = cta_tmem_begin<PL::TCOLS1>(tslot, warp);
+    t_tw = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * PL::TW1);
+    // this lane's twiddles W_N1^{q1 p}, p < P
+    sfor<0, PL::TW1 / 16>([&](auto c_) {
+      constexpr int cc = decltype(c_)::value;
+      float w16[16];
+      sfor<0, 8>([&](auto k_) {
+        constexpr int k = decltype(k_)::value;
+        const float2 w = tw_small<N1>(q1 * (8 * cc + k));
+        w16[2 * k] = w.x;
+        w16[2 * k + 1] = w.y;
+      });
+      tmem_st16(t_tw + 16 * cc, w16);
+    });
+    tmem_wait_st();
+  }
+
+  // the second half of the work on one column group: twiddle, transpose, Q1-point DFTs, store
+  auto finish = [&](float2 (&v)[P], bool act, long long g, long long b) {
+    dit<P>(v);
+    if constexpr (Q1 > 1) {
+      sfor<0, P / 8>([&](auto c_) {
+        constexpr int cc = decltype(c_)::value;
+        float w16[16];
+        tmem_ld16(t_tw + 16 * cc, w16);
+        tmem_wait_ld();
+        sfor<0, 8>([&](auto k_) {
+          constexpr int k = decltype(k_)::value;
+          constexpr int p = 8 * cc + k;
+          if constexpr (p > 0) v[p] = cmul(v[p], make_float2(w16[2 * k], w16[2 * k + 1]));
+        });
+      });
+      sfor<0, P>([&](auto p_) {
+        constexpr int p = decltype(p_)::value;
+        region[q1 * LDQ + p * LDP + cw] = v[p];
+      });
+      __syncwarp();
+      sfor<0, PQ>([&](auto r_) {
+        constexpr int r = decltype(r_)::value;
+        const int p = q1 * PQ + r;
+        float2 u[Q1];
+        sfor<0, Q1>([&](auto q_) {
+          constexpr int q = decltype(q_)::value;
+          u[ct::bitrev(q, Q1)] = region[q * LDQ + p * LDP + cw];
+        });
+        dit<Q1>(u);
+        if (act) {
+          float2* dst = a.scratch + ((size_t)g * N1 + p) * N2 + b;
+          sfor<0, Q1>([&](auto m_) {
+            constexpr int m = decltype(m_)::value;
+            dst[(size_t)m * P * N2] = u[m];
+          });
+        }
+      });
+      __syncwarp();  // region free for the next item
+    } else {
+      if (act) {
+        float2* dst = a.scratch + (size_t)g * N1 * N2 + b;
+        sfor<0, P>([&](auto p_) {
+          constexpr int p = decltype(p_)::value;
+          dst[(size_t)p * N2] = v[p];
+        });
+      }
+    }
+  };
+
+  const long long total_cols = (long long)a.nseg * a.n_fpair * N2;
+  if constexpr (!STAGED) {
+    // small N: each warp item = CW global columns, each lane loads its own words
+    const long long n_items = (total_cols + CW - 1) / CW;
+    const long long nw = (long long)gridDim.x * PL::WARPS;
+    for (long long item = (long long)blockIdx.x * PL::WARPS + warp; item < n_items; item += nw) {
+      const long long gc = item * CW + cw;
+      const bool act = gc < total_cols;
+      const long long g = gc / N2, b = gc % N2;
+      float2 v[P];
+      if (act) {
+        p1_load<LOGN, BITS>(a, (int)g, (int)b, q1, v);
+      } else {
+        sfor<0, P>([&](auto t_) { v[decltype(t_)::value] = make_float2(0.f, 0.f); });
+      }
+      finish(v, act, g, b);
+    }
+  } else {
+    // CTA tiles of TILE columns of one pair-segment.  The packed words of a tile (both IFs)
+    // are staged in shared memory with cp.async, double-buffered so that the next tile's
+    // words are in flight while the warps work on this one; every warp decodes its CW
+    // columns from the stage.
+    constexpr int RS = PL::template stage_row<BITS>();  // words per staged row (odd: no conflicts)
+    constexpr int SB = N1 * RS;                         // words per stage buffer
+    const long long n_tiles = total_cols / TILE;
+    const uint32_t stage_a = smem_addr(stage);
+    auto issue = [&](long long tile, int buf) {
+      const long long gc0 = tile * TILE;
+      const int g = (int)(gc0 / N2), b0 = (int)(gc0 % N2);
+      const int s_local = g / a.n_fpair, f = g - s_local * a.n_fpair;
+      const int sg = a.seg0 + s_local;
+      const int ia = a.fa[f], ib = a.fb[f];
+      const uint32_t* pa = seg_ptr(a.in, ia, sg) + (b0 * BITS) / 32;
+      const uint32_t* pb = ib >= 0 ? seg_ptr(a.in, ib, sg) + (b0 * BITS) / 32 : nullptr;
+      const uint32_t dst0 = stage_a + 4u * (uint32_t)(buf * SB);
+      for (int k = threadIdx.x; k < N1 * WPR; k += PL::THREADS) {
+        const int row = k / WPR, wd = k % WPR;
+        const size_t off = (size_t)row * (N2 * BITS / 32) + wd;
+        cp_async4(dst0 + 4u * (uint32_t)(row * RS + wd), pa + off);
+        if (pb) cp_async4(dst0 + 4u * (uint32_t)(row * RS + WPR + wd), pb + off);
+      }
+      cp_async_commit();
+    };
+    long long tile = blockIdx.x;
+    if (tile < n_tiles) issue(tile, 0);
+    for (int buf = 0; tile < n_tiles; tile += gridDim.x, buf ^= 1) {
+      cp_async_wait_all();
+      __syncthreads();  // this tile's words are staged; every warp is done with the other buffer
+      if (tile + gridDim.x < n_tiles) issue(tile + gridDim.x, buf ^ 1);
+      const long long gc0 = tile * TILE;
+      const int g = (int)(gc0 / N2), b0 = (int)(gc0 % N2);
+      const int f = g % a.n_fpair;
+      const bool has_b = a.fb[f] >= 0;
+      const int col = warp * CW + cw;  // column inside the tile
+      const long long b = b0 + col;
+      const int wd = (col * BITS) >> 5;
+      const uint32_t shift = (uint32_t)((col * BITS) & 31);
+      const uint32_t* sb = stage + buf * SB;
+      const float* taps = a.taps;
+      float2 v[P];
+      sfor<0, P>([&](auto t_) {
+        constexpr int t = decltype(t_)::value;
+        const int row = q1 + Q1 * t;
+        float x = decode_level<BITS>(sb[row * RS + wd], shift);
+        float y = has_b ? decode_level<BITS>(sb[row * RS + WPR + wd], shift) : 0.0f;
+        if (taps) {
+          const float tv = __ldg(taps + row * N2 + b);
+          x *= tv;
+          y *= tv;
+        }
+        v[ct::bitrev(t, P)] = make_float2(x, y);
+      });
+      finish(v, true, g, b);
+    }
+    cp_async_wait_all();
+  }
+  if constexpr (Q1 > 1) cta_tmem_end<PL::TCOLS1>(tbase, warp);
+}
+
+// ------------------------------------------------------------------------------------------
+// phase 2 and the correlator.  A warp owns UPW units (column u and its mirror N1 - u; unit 0
+// = columns 0 and N1/2) over a range of segments.  Lane (uw, e, q2) loads rows q2 + Q2 t of
+// its column, applies W_N^{b u} (its tensor-memory twiddles; the mirror conjugated), runs the
+// P-point DFT, transposes through the warp's region (the two members of a unit together),
+// applies W_N2^{q p} and runs the Q2-point DFTs, so that lane (uw, j) holds Z_k and
+// conj(Z_{N-k}) for bins k = u + N1 d, d = j PP + r + P m.  |S|^2, |D|^2 and i S conj(D)
+// (S = 2X, D = 2iY) are accumulated in its tensor-memory lane over the range and added once
+// to the integration accumulators.
+// ------------------------------------------------------------------------------------------
+template <int LOGN>
+__global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, int range_len) {
+  using PL = Plan<LOGN>;
+  constexpr int P = PL::P, N1 = PL::N1, N2 = PL::N2, Q2 = PL::Q2, UPS = PL::UPS, UPW = PL::UPW;
+  constexpr int SL = PL::SL, UGW = PL::UGW, PP = PL::PP, NACC = PL::NACC;
+  constexpr int LDQ = PL::LDQ2, LDE = PL::LDE2, TACC = PL::TACC;
+  extern __shared__ float2 sm2[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float2* region = sm2 + warp * PL::REGION2;
+  float2* tw2 = sm2 + PL::WARPS * PL::REGION2;  // skewed table: W_N2^k at k + k/32
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(tw2 + PL::TWT);
+
+  // lane roles: step 1 (uw, e, q2); step 2 (uw, j)
+  const int uw = lane / (2 * Q2), e1 = (lane / Q2) & 1, q2 = lane % Q2, j = lane % (2 * Q2);
+  const int so = (SL > 1) ? uw / UPS : 0;
+  const int uoff = (SL > 1) ? uw % UPS : uw;
+
+  for (int k = tid; k < N2; k += PL::THREADS) tw2[k + (k >> 5)] = tw_small<N2>(k);
+  const uint32_t tbase = cta_tmem_begin<PL::TCOLS2>(tslot, warp);  // (its barrier also publishes tw2)
+  const uint32_t t_acc = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * (PL::TCOLS2 / 2));
+  const uint32_t t_tw = t_acc + TACC;
+
+  const int R = (a.nseg + SL - 1) / SL;                // rounds of SL segments
+  const int NRG = (R + range_len - 1) / range_len;     // ranges per (pair, unit group)
+  const long long n_items = (long long)a.n_fpair * UGW * NRG;
+  const long long nw = (long long)gridDim.x * PL::WARPS;
+  for (long long item = (long long)blockIdx.x * PL::WARPS + warp; item < n_items; item += nw) {
+    const int rg = (int)(item % NRG);
+    const int fug = (int)(item / NRG);
+    const int ug = fug % UGW, f = fug / UGW;
+    const int u = (SL > 1) ? uoff : ug * UPW + uoff;
+    const int c = (u == 0) ? (e1 ? N1 / 2 : 0) : (e1 ? N1 - u : u);
+    const int tu = (u == 0 && e1) ? N1 / 2 : u;
+    const float sgn = (e1 && u != 0) ? -1.0f : 1.0f;
+    const bool special = (u == 0);
+    const bool warp_special = (SL > 1) || (ug == 0);  // some lane of this warp holds unit 0
+    // tensor memory: zero the accumulators, load this lane's twiddles W_N^{b tu}, b = q2 + Q2 t
+    sfor<0, TACC / 16>([&](auto c_) {
+      constexpr int cc = decltype(c_)::value;
+      float z16[16];
+      sfor<0, 16>([&](auto k_) { z16[decltype(k_)::value] = 0.f; });
+      tmem_st16(t_acc + 16 * cc, z16);
+    });
+    sfor<0, PL::TTW / 16>([&](auto c_) {
+      constexpr int cc = decltype(c_)::value;
+      float w16[16];
+      sfor<0, 8>([&](auto k_) {
+        constexpr int k = decltype(k_)::value;
+        constexpr int t = 8 * cc + k;
+        float2 w = make_float2(0.f, 0.f);
+        if constexpr (t < P) w = __ldg(a.tw + (size_t)(q2 + Q2 * t) * (UPS + 1) + tu);
+        w16[2 * k] = w.x;
+        w16[2 * k + 1] = w.y;
+      });
+      tmem_st16(t_tw + 16 * cc, w16);
+    });
+    tmem_wait_st();
+    float extra[4] = {0.f, 0.f, 0.f, 0.f};
+    bool worked = false;
+    const int r_end = min(R, (rg + 1) * range_len);
+    for (int rnd = rg * range_len; rnd < r_end; ++rnd) {
+      const int s = rnd * SL + so;
+      const bool act = s < a.nseg;
+      worked |= act;
+      // step 1: load the column, twiddle, P-point DFT
+      const float2* src = a.scratch + ((size_t)(act ? s : 0) * a.n_fpair + f) * N1 * N2 + (size_t)c * N2 + q2;
+      float2 v[P];
+      sfor<0, P>([&](auto t_) {
+        constexpr int t = decltype(t_)::value;
+        v[ct::bitrev(t, P)] = act ? __ldcg(src + Q2 * t) : make_float2(0.f, 0.f);
+      });
+      sfor<0, (P + 7) / 8>([&](auto c_) {
+        constexpr int cc = decltype(c_)::value;
+        float w16[16];
+        tmem_ld16(t_tw + 16 * cc, w16);
+        tmem_wait_ld();
+        sfor<0, 8>([&](auto k_) {
+          constexpr int k = decltype(k_)::value;
+          constexpr int t = 8 * cc + k;
+          if constexpr (t < P) {
+            float2 z = v[ct::bitrev(t, P)];
+            z.y *= sgn;  // mirror column: conjugate
+            v[ct::bitrev(t, P)] = cmul(z, make_float2(w16[2 * k], w16[2 * k + 1]));
+          }
+        });
+      });
+      dit<P>(v);
+      // joint transpose through the warp's region
+      sfor<0, P>([&](auto p_) {
+        constexpr int p = decltype(p_)::value;
+        region[(uw * 2 + e1) * LDE + p * LDQ + q2] = v[p];
+      });
+      __syncwarp();
+      float2 wv[2 * PP * Q2];
+      sfor<0, PP>([&](auto r_) {
+        constexpr int r = decltype(r_)::value;
+        const int p = j * PP + r;
+        sfor<0, Q2>([&](auto q_) {
+          constexpr int q = decltype(q_)::value;
+          float2 w = make_float2(1.f, 0.f);
+          if constexpr (q > 0) {
+            const int k = (q * p) & (N2 - 1);
+            w = tw2[k + (k >> 5)];
+          }
+          sfor<0, 2>([&](auto e_) {
+            constexpr int e = decltype(e_)::value;
+            const float2 z = region[(uw * 2 + e) * LDE + p * LDQ + q];
+            wv[(e * PP + r) * Q2 + ct::bitrev(q, Q2)] = (q > 0) ? cmul(z, w) : z;
+          });
+        });
+        sfor<0, 2>([&](auto e_) {
+          constexpr int e = decltype(e_)::value;
+          dit<Q2, (e * PP + r) * Q2, 1>(wv);
+        });
+      });
+      __syncwarp();  // region consumed
+      float2* s0 = region + (uw * 2 + 0) * N2;  // unit 0 mirror exchange: column 0
+      float2* sh = region + (uw * 2 + 1) * N2;  //                         column N1/2
+      if (warp_special) {
+        if (special) {
+          sfor<0, 2>([&](auto e_) {
+            constexpr int e = decltype(e_)::value;
+            sfor<0, PP>([&](auto r_) {
+              constexpr int r = decltype(r_)::value;
+              sfor<0, Q2>([&](auto m_) {
+                constexpr int m = decltype(m_)::value;
+                region[(uw * 2 + e) * N2 + j * PP + r + P * m] = wv[(e * PP + r) * Q2 + m];
+              });
+            });
+          });
+        }
+        __syncwarp();
+      }
+      // correlate into the tensor-memory accumulators
+      sfor<0, (NACC + 3) / 4>([&](auto c_) {
+        constexpr int cc = decltype(c_)::value;
+        float a16[16];
+        tmem_ld16(t_acc + 16 * cc, a16);
+        tmem_wait_ld();
+        if (act) {
+          sfor<0, 4>([&](auto k_) {
+            constexpr int slot = 4 * cc + decltype(k_)::value;
+            if constexpr (slot < NACC) {
+              constexpr int r = slot / Q2, m = slot % Q2;
+              float(&q)[4] = *reinterpret_cast<float(*)[4]>(a16 + 4 * (slot - 4 * cc));
+              if (!special) {
+                corr_acc(q, wv[r * Q2 + m], wv[(PP + r) * Q2 + m]);
+              } else {
+                const int d = j * PP + r + P * m;
+                float2 Uv, Vv;
+                if (d <= N2 / 2) {  // column 0: bins N1 d, mirror N1 (N2 - d)
+                  Uv = s0[d];
+                  const float2 t = s0[(N2 - d) & (N2 - 1)];
+                  Vv = make_float2(t.x, -t.y);
+                } else {  // column N1/2 at dh = d - N2/2 - 1: bins N1/2 + N1 dh, mirror N2 - 1 - dh
+                  const int dh = d - N2 / 2 - 1;
+                  Uv = sh[dh];
+                  const float2 t = sh[N2 - 1 - dh];
+                  Vv = make_float2(t.x, -t.y);
+                }
+                corr_acc(q, Uv, Vv);
+              }
+            }
+          });
+        }
+        tmem_st16(t_acc + 16 * cc, a16);
+      });
+      tmem_wait_st();
+      if (act && special && j == 0) {  // the one extra bin: column N1/2 at dh = N2/2 - 1
+        const float2 t = sh[N2 / 2];
+        corr_acc(extra, sh[N2 / 2 - 1], make_float2(t.x, -t.y));
+      }
+      if (warp_special) __syncwarp();  // mirror area read before the next transpose
+    }
+    // flush this lane's sums into the integration accumulators (native order)
+    const size_t base = (size_t)f * PL::NATIVE;
+    sfor<0, (NACC + 3) / 4>([&](auto c_) {
+      constexpr int cc = decltype(c_)::value;
+      float a16[16];
+      tmem_ld16(t_acc + 16 * cc, a16);
+      tmem_wait_ld();
+      if (worked) {
+        sfor<0, 4>([&](auto k_) {
+          constexpr int slot = 4 * cc + decltype(k_)::value;
+          if constexpr (slot < NACC) {
+            constexpr int r = slot / Q2, m = slot % Q2;
+            const int d = j * PP + r + P * m;
+            const float* q = a16 + 4 * (slot - 4 * cc);
+            const size_t o = base + (size_t)u * N2 + d;
+            if (!a.fp64) {
+              atomicAdd(reinterpret_cast<float4*>(a.acc) + o, make_float4(q[0], q[1], q[2], q[3]));
+            } else {
+              double* op = reinterpret_cast<double*>(a.acc) + 4 * o;
+              atomicAdd(op + 0, (double)q[0]);
+              atomicAdd(op + 1, (double)q[1]);
+              atomicAdd(op + 2, (double)q[2]);
+              atomicAdd(op + 3, (double)q[3]);
+            }
+          }
+        });
+      }
+    });
+    if (worked && special && j == 0) {
+      const size_t o = base + (size_t)UPS * N2;
+      if (!a.fp64) {
+        atomicAdd(reinterpret_cast<float4*>(a.acc) + o, make_float4(extra[0], extra[1], extra[2], extra[3]));
+      } else {
+        double* op = reinterpret_cast<double*>(a.acc) + 4 * o;
+        atomicAdd(op + 0, (double)extra[0]);
+        atomicAdd(op + 1, (double)extra[1]);
+        atomicAdd(op + 2, (double)extra[2]);
+        atomicAdd(op + 3, (double)extra[3]);
+      }
+    }
+  }
+  cta_tmem_end<PL::TCOLS2>(tbase, warp);
+}
+
+// ------------------------------------------------------------------------------------------
+// host-side launchers (instantiated once per N): persistent grids, as many CTAs as fit
+// ------------------------------------------------------------------------------------------
+// CTAs of `kernel` that fit on one SM at once: the larger of the occupancy API's answer and
+// a direct count from the kernel's registers and shared memory (the API has been seen to
+// return 1 for these kernels although two fit).  The kernels never wait on one another, so
+// a CTA beyond what fits simply starts later.
+template <typename K>
+static int ctas_per_sm(K kernel, int threads, size_t smem) {
+  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) {
+    cudaGetLastError();
+    n = 0;
+  }
+  cudaFuncAttributes fa;
+  int manual = 1;
+  int dev = 0, regs_sm = 65536, smem_sm = 233472;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+  cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (cudaFuncGetAttributes(&fa, kernel) == cudaSuccess && fa.numRegs > 0) {
+    const int by_regs = regs_sm / (fa.numRegs * threads);
+    const int by_smem = smem_sm / (int)(smem + fa.sharedSizeBytes + 1024);
+    const int by_threads = 2048 / threads;
+    manual = by_regs < by_smem ? by_regs : by_smem;
+    manual = manual < by_threads ? manual : by_threads;
+    if (manual > 2) manual = 2;  // tensor memory: at most two CTAs of 256 columns per SM
+  } else {
+    cudaGetLastError();
+  }
+  n = n > manual ? n : manual;
+  return n < 1 ? 1 : n;
+}
+
 template <int LOGN, int BITS>
 static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st) {
   using PL = Plan<LOGN>;
-  static int attr_dev = -1;
+  static int attr_dev = -1, per_sm = 1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (attr_dev != dev) {
-    cudaError_t e = cudaFuncSetAttribute(k_phase1<LOGN, BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::SMEM1);
+    cudaError_t e = cudaFuncSetAttribute(k_phase1<LOGN, BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)PL::template smem1<BITS>());
     if (e != cudaSuccess) return e;
+    per_sm = ctas_per_sm(k_phase1<LOGN, BITS>, PL::THREADS, PL::template smem1<BITS>());
     attr_dev = dev;
   }
-  const long long cols = (long long)a.nseg * a.n_fpair * PL::N2;
-  const int grid = (int)((cols + PL::W - 1) / PL::W);
-  k_phase1<LOGN, BITS><<<grid, PL::T1, PL::SMEM1, st>>>(a);
+  const long long items = ((long long)a.nseg * a.n_fpair * PL::N2 + PL::CW - 1) / PL::CW;
+  const long long ctas = (items + PL::WARPS - 1) / PL::WARPS;  // = tiles when staged
+  const long long cap = (long long)per_sm * a.num_sms;
+  k_phase1<LOGN, BITS><<<(int)(ctas < cap ? ctas : cap), PL::THREADS, PL::template smem1<BITS>(), st>>>(a);
   return cudaGetLastError();
 }
 
@@ -388,28 +656,29 @@ cudaError_t run_phase1(const BatchArgs& a, cudaStream_t st) {
   }
 }
 
-// phase 2 of one batch: tiles = (FFT pair, unit block, chunk of segments), ~2 tiles per SM
+// phase 2 of one batch: items (pair, unit group, range of segments), about one per warp
 template <int LOGN>
 cudaError_t run_phase2(const BatchArgs& a, cudaStream_t st) {
   using PL = Plan<LOGN>;
   if (a.nseg <= 0) return cudaSuccess;
-  static int attr_dev = -1;
+  static int attr_dev = -1, per_sm = 1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (attr_dev != dev) {
     cudaError_t e = cudaFuncSetAttribute(k_phase2<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::SMEM2);
     if (e != cudaSuccess) return e;
+    per_sm = ctas_per_sm(k_phase2<LOGN>, PL::THREADS, PL::SMEM2);
     attr_dev = dev;
   }
-  const int per_chunk_tiles = a.n_fpair * PL::NUB;
-  const int max_chunks = (a.nseg + PL::SLOTS - 1) / PL::SLOTS;
-  int want = (2 * a.num_sms + per_chunk_tiles - 1) / per_chunk_tiles;
-  if (want < 1) want = 1;
-  if (want > max_chunks) want = max_chunks;
-  int seg_per_tile = (a.nseg + want - 1) / want;
-  seg_per_tile = ((seg_per_tile + PL::SLOTS - 1) / PL::SLOTS) * PL::SLOTS;
-  const int n_chunks = (a.nseg + seg_per_tile - 1) / seg_per_tile;
-  k_phase2<LOGN><<<per_chunk_tiles * n_chunks, PL::T2, PL::SMEM2, st>>>(a, seg_per_tile, n_chunks);
+  const long long warps = (long long)per_sm * a.num_sms * PL::WARPS;
+  const int R = (a.nseg + PL::SL - 1) / PL::SL;
+  const long long groups = (long long)a.n_fpair * PL::UGW;
+  long long range_len = (groups * R + warps - 1) / warps;  // rounds per item
+  if (range_len < 1) range_len = 1;
+  const long long n_items = groups * ((R + range_len - 1) / range_len);
+  const long long ctas = (n_items + PL::WARPS - 1) / PL::WARPS;
+  const long long cap = (long long)per_sm * a.num_sms;
+  k_phase2<LOGN><<<(int)(ctas < cap ? ctas : cap), PL::THREADS, PL::SMEM2, st>>>(a, (int)range_len);
   return cudaGetLastError();
 }
 

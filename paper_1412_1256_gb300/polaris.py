@@ -15,7 +15,8 @@ import threading
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libpolaris.so")
+# POLARIS_LIB selects another build of the library (e.g. a tuning variant)
+LIB_PATH = os.environ.get("POLARIS_LIB") or os.path.join(HERE, "libpolaris.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT = 0, -1, -2, -3, -4, -5
 WIN_RECT, WIN_HANN, WIN_CUSTOM = 0, 1, 2
