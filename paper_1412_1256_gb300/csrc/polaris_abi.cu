@@ -68,7 +68,7 @@ __global__ void k_unpack(const uint32_t* __restrict__ w, long long n, float* __r
 // Each slot holds sum |S|^2, |D|^2 and Re, Im of i S conj(D) with S = 2X, D = 2iY.
 // ---------------------------------------------------------------------------------------
 struct ReadoutArgs {
-  const void* acc;
+  void* acc;  // read, then cleared
   int fp64;
   int N1, N2, UPS, nbin, native;
   int fa[kMaxIF], fb[kMaxIF], fcorr[kMaxIF];
@@ -80,67 +80,110 @@ struct ReadoutArgs {
   float inv_ga2[kMaxIF], inv_gb2[kMaxIF], ig_re[kMaxIF], ig_im[kMaxIF];  // 1/|Ga|^2, 1/|Gb|^2, 1/(Ga conj Gb)
 };
 
-__global__ void k_readout(ReadoutArgs a) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x, f = blockIdx.y;
-  if (k >= a.nbin) return;
-  const int c = k & (a.N1 - 1), d = k / a.N1;
-  int idx;
-  bool cj = false;
-  if (c == 0) idx = d;
-  else if (c == a.N1 / 2) idx = (d <= a.N2 / 2 - 2) ? a.N2 / 2 + 1 + d : a.UPS * a.N2;
-  else if (c < a.N1 / 2) idx = c * a.N2 + d;
-  else {
-    idx = (a.N1 - c) * a.N2 + (a.N2 - 1 - d);
-    cj = true;
-  }
-  const size_t off = (size_t)f * a.native + idx;
-  float xx, yy, xr, xi;
-  if (a.fp64) {
-    const double* p = reinterpret_cast<const double*>(a.acc) + 4 * off;
-    xx = (float)(0.25 * p[0]);
-    yy = (float)(0.25 * p[1]);
-    xr = (float)(0.25 * p[2]);
-    xi = (float)(0.25 * p[3]);
-  } else {
-    const float4 v = reinterpret_cast<const float4*>(a.acc)[off];
-    xx = 0.25f * v.x;
-    yy = 0.25f * v.y;
-    xr = 0.25f * v.z;
-    xi = 0.25f * v.w;
-  }
-  if (cj) xi = -xi;
-  if (a.autos) {
-    a.autos[(size_t)a.fa[f] * a.nbin + k] = xx;
-    if (a.fb[f] >= 0) a.autos[(size_t)a.fb[f] * a.nbin + k] = yy;
-  }
-  const int p = a.fcorr[f];
-  if (p < 0) return;
-  if (a.cross) {
-    a.cross[((size_t)p * a.nbin + k) * 2 + 0] = xr;
-    a.cross[((size_t)p * a.nbin + k) * 2 + 1] = xi;
-  }
-  if (a.stokes) {
-    const float x = xx * a.inv_ga2[p], y = yy * a.inv_gb2[p];
-    const float cr = xr * a.ig_re[p] - xi * a.ig_im[p];
-    const float ci = xr * a.ig_im[p] + xi * a.ig_re[p];
-    float I, Q, Uq, V;
-    if (a.feed == POLARIS_FEED_LINEAR) {
-      I = 0.5f * (x + y);
-      Q = 0.5f * (a.c2 * (x - y) - a.s2 * 2.0f * cr);
-      Uq = 0.5f * (a.s2 * (x - y) + a.c2 * 2.0f * cr);
-      V = ci;
-    } else {
-      I = 0.5f * (x + y);
-      V = 0.5f * (x - y);
-      Q = a.c2 * cr - a.s2 * ci;
-      Uq = a.s2 * cr + a.c2 * ci;
+// Readout of one block: TD consecutive values of d times all N1 values of c, i.e. the natural
+// bins k = c + N1 d in [N1 d0, N1 (d0 + TD)).  Reads walk the native layout along d (runs of TD
+// consecutive or reversed slots per c), writes walk k; a padded shared tile turns one into the
+// other.  The map k -> native slot is a bijection, so the block also clears the slots it read:
+// the accumulators start the next integration at zero without a separate memset.
+constexpr int kReadoutMinTile = 512;  // natural bins per block (at least N1; TD >= 2 at N1 <= 256)
+constexpr int kReadoutThreads = 256;
+constexpr int kReadoutPerThread = 4;  // covers N1 <= 1024
+
+__global__ void __launch_bounds__(kReadoutThreads) k_readout(ReadoutArgs a) {
+  __shared__ float4 tile[1024 + 128];  // TD (N1 + 1) <= TE + TD entries; TE <= 1024, TD <= 128
+  const int f = blockIdx.y, N1 = a.N1, N2 = a.N2;
+  const int TD = N1 >= kReadoutMinTile ? 1 : kReadoutMinTile / N1, TE = TD * N1;
+  const int d0 = blockIdx.x * TD;
+  const size_t fo = (size_t)f * a.native;
+  int slot[kReadoutPerThread], sidx[kReadoutPerThread];
+  bool cjv[kReadoutPerThread];
+  float4 v[kReadoutPerThread];
+  // all loads first (several in flight per thread), then the clears and the shared stores
+#pragma unroll
+  for (int i = 0; i < kReadoutPerThread; ++i) {
+    const int e = threadIdx.x + i * kReadoutThreads;
+    slot[i] = -1;
+    const int c = e / TD, dd = e - c * TD, d = d0 + dd;
+    const int k = c + N1 * d;
+    if (e >= TE || k >= a.nbin) continue;
+    int idx;
+    bool cj = false;
+    if (c == 0) idx = d;
+    else if (c == N1 / 2) idx = (d <= N2 / 2 - 2) ? N2 / 2 + 1 + d : a.UPS * N2;
+    else if (c < N1 / 2) idx = c * N2 + d;
+    else {
+      idx = (N1 - c) * N2 + (N2 - 1 - d);
+      cj = true;
     }
-    float* o = a.stokes + (size_t)p * 4 * a.nbin + k;
-    o[0] = I;
-    o[a.nbin] = Q;
-    o[2 * (size_t)a.nbin] = Uq;
-    o[3 * (size_t)a.nbin] = V;
+    slot[i] = idx;
+    sidx[i] = dd * (N1 + 1) + c;
+    cjv[i] = cj;
+    if (a.fp64) {
+      const double4 w = reinterpret_cast<const double4*>(a.acc)[fo + idx];
+      v[i] = make_float4((float)(0.25 * w.x), (float)(0.25 * w.y), (float)(0.25 * w.z), (float)(0.25 * w.w));
+    } else {
+      const float4 w = reinterpret_cast<const float4*>(a.acc)[fo + idx];
+      v[i] = make_float4(0.25f * w.x, 0.25f * w.y, 0.25f * w.z, 0.25f * w.w);
+    }
   }
+#pragma unroll
+  for (int i = 0; i < kReadoutPerThread; ++i) {
+    if (slot[i] < 0) continue;
+    if (a.fp64) reinterpret_cast<double4*>(a.acc)[fo + slot[i]] = make_double4(0.0, 0.0, 0.0, 0.0);
+    else reinterpret_cast<float4*>(a.acc)[fo + slot[i]] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 t = v[i];
+    if (cjv[i]) t.w = -t.w;
+    tile[sidx[i]] = t;
+  }
+  __syncthreads();
+  const int p = a.fcorr[f];
+  float* autos_a = a.autos ? a.autos + (size_t)a.fa[f] * a.nbin : nullptr;
+  float* autos_b = (a.autos && a.fb[f] >= 0) ? a.autos + (size_t)a.fb[f] * a.nbin : nullptr;
+  float2* cross = (a.cross && p >= 0) ? reinterpret_cast<float2*>(a.cross) + (size_t)p * a.nbin : nullptr;
+  float* stokes = (a.stokes && p >= 0) ? a.stokes + (size_t)p * 4 * a.nbin : nullptr;
+  float inv_ga2 = 0.f, inv_gb2 = 0.f, ig_re = 0.f, ig_im = 0.f;
+  if (p >= 0) {
+    inv_ga2 = a.inv_ga2[p];
+    inv_gb2 = a.inv_gb2[p];
+    ig_re = a.ig_re[p];
+    ig_im = a.ig_im[p];
+  }
+  for (int e = threadIdx.x; e < TE; e += kReadoutThreads) {
+    const int k = N1 * d0 + e;
+    if (k >= a.nbin) break;
+    const int dd = e / N1, c = e - dd * N1;
+    const float4 v = tile[dd * (N1 + 1) + c];
+    const float xx = v.x, yy = v.y, xr = v.z, xi = v.w;
+    if (autos_a) autos_a[k] = xx;
+    if (autos_b) autos_b[k] = yy;
+    if (cross) cross[k] = make_float2(xr, xi);
+    if (stokes) {
+      const float x = xx * inv_ga2, y = yy * inv_gb2;
+      const float cr = xr * ig_re - xi * ig_im;
+      const float ci = xr * ig_im + xi * ig_re;
+      float I, Q, Uq, V;
+      if (a.feed == POLARIS_FEED_LINEAR) {
+        I = 0.5f * (x + y);
+        Q = 0.5f * (a.c2 * (x - y) - a.s2 * 2.0f * cr);
+        Uq = 0.5f * (a.s2 * (x - y) + a.c2 * 2.0f * cr);
+        V = ci;
+      } else {
+        I = 0.5f * (x + y);
+        V = 0.5f * (x - y);
+        Q = a.c2 * cr - a.s2 * ci;
+        Uq = a.s2 * cr + a.c2 * ci;
+      }
+      stokes[k] = I;
+      stokes[a.nbin + k] = Q;
+      stokes[2 * (size_t)a.nbin + k] = Uq;
+      stokes[3 * (size_t)a.nbin + k] = V;
+    }
+  }
+}
+
+static dim3 readout_grid(int N1, int N2, int n_fpair) {
+  const int td = N1 >= kReadoutMinTile ? 1 : kReadoutMinTile / N1;
+  return dim3((unsigned)((N2 / 2 + 1 + td - 1) / td), (unsigned)n_fpair);
 }
 
 static int host_plan_n2(int logn) { return 1 << plan_log_n2(logn); }
@@ -666,13 +709,12 @@ extern "C" int spectrometer_integrate_device(polaris_spec* s, const polaris_stok
   r.autos = d_autos;
   r.cross = d_cross;
   r.stokes = d_stokes;
-  dim3 grid((unsigned)((s->nbin + 255) / 256), (unsigned)s->n_fpair);
+  const dim3 grid = readout_grid(s->N1, s->N2, s->n_fpair);
   CUDA_OR_FAIL(s, counted_launch(s, 2, st, [&]() {
-                  k_readout<<<grid, 256, 0, st>>>(r);
+                  k_readout<<<grid, kReadoutThreads, 0, st>>>(r);
                   return cudaGetLastError();
                 }));
-  const size_t acc_bytes = (size_t)s->n_fpair * s->native * 4 * (s->accum_fp64 ? 8 : 4);
-  CUDA_OR_FAIL(s, cudaMemsetAsync(s->d_acc, 0, acc_bytes, st));
+  // (the readout has cleared the accumulators it read)
   if (n_segments_out) *n_segments_out = s->seg_acc;
   s->seg_acc = 0;
   return POLARIS_OK;
@@ -985,8 +1027,7 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
   r.autos = d_autos;
   r.cross = n_pair ? d_cross : nullptr;
   r.stokes = n_pair ? d_stokes : nullptr;
-  dim3 grid((unsigned)((r.nbin + 255) / 256), (unsigned)nf);
-  k_readout<<<grid, 256, 0, st>>>(r);
+  k_readout<<<readout_grid(r.N1, r.N2, nf), kReadoutThreads, 0, st>>>(r);
   e = cudaGetLastError();
   if (e != cudaSuccess) return set_err(nullptr, POLARIS_ECUDA, "no-alloc readout: %s", cudaGetErrorString(e));
   if (n_segments_out) *n_segments_out = nseg;

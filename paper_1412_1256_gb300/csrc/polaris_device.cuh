@@ -185,11 +185,13 @@ constexpr int plan_log_n2(int logn) {
 }
 // ----------------------------------------------------------------------------------------
 // shared-memory layouts of the warp-local transposes.  The strides below were chosen by an
-// offline simulation of the bank conflicts of each transpose's write and read patterns
-// (8-byte elements; a warp access costs max over the 16 bank pairs of the distinct elements
-// that fall on it): they give the minimum of 2 wavefronts per access for the phase-1
-// layouts and for phase 2 at Q2 = 16 and Q2 = 2 with P = 4, and at most 4 otherwise.
-//   phase 1, element (q, p, cw) at q * LDQ1 + p * LDP1 + cw
+// offline simulation of the bank conflicts of each transpose's write and read patterns.
+// An 8-byte warp access is served as two half-warps; each half costs the largest number of
+// distinct elements that fall on one of the 16 bank pairs (this model reproduces the
+// measured wavefront counts).  All phase-1 layouts reach the minimum of 2 wavefronts per
+// access; phase 2 reaches it at Q2 = 16 and P = 4, Q2 = 2, and costs at most 4 otherwise.
+//   phase 1, element (q, p, cw) at q * LDQ1 + p * LDP1 + cw; written by lane (q, cw) for all
+//            p, read by lane (q1, cw) for p = r Q1 + q1, then reused as the [c][cw] output tile
 //   phase 2, element (unit, e, p, q) at (unit * 2 + e) * LDE2 + p * LDQ2 + q
 // ----------------------------------------------------------------------------------------
 namespace bank {
@@ -198,23 +200,23 @@ struct Ld2 {
 };
 constexpr Ld2 p1_layout(int P, int Q1) {
   return (P == 32 && Q1 == 2)    ? Ld2{16, 512}
-         : (P == 32 && Q1 == 4)  ? Ld2{9, 292}
-         : (P == 32 && Q1 == 8)  ? Ld2{5, 162}
-         : (P == 32 && Q1 == 16) ? Ld2{3, 97}
+         : (P == 32 && Q1 == 4)  ? Ld2{8, 264}
+         : (P == 32 && Q1 == 8)  ? Ld2{4, 132}
+         : (P == 32 && Q1 == 16) ? Ld2{2, 66}
          : (P == 32 && Q1 == 32) ? Ld2{1, 33}
                                  : Ld2{32 / Q1, P * (32 / Q1)};  // Q1 = 1: no transpose
 }
 constexpr Ld2 p2_layout(int P, int Q2) {
   return (P == 32 && Q2 == 16)  ? Ld2{17, 544}
-         : (P == 32 && Q2 == 8) ? Ld2{9, 288}
-         : (P == 32 && Q2 == 4) ? Ld2{5, 161}
-         : (P == 32 && Q2 == 2) ? Ld2{2, 65}
+         : (P == 32 && Q2 == 8) ? Ld2{9, 296}
+         : (P == 32 && Q2 == 4) ? Ld2{5, 163}
+         : (P == 32 && Q2 == 2) ? Ld2{3, 95}
          : (P == 32 && Q2 == 1) ? Ld2{1, 33}
          : (P == 16 && Q2 == 2) ? Ld2{2, 33}
          : (P == 16 && Q2 == 1) ? Ld2{1, 17}
-         : (P == 8 && Q2 == 2)  ? Ld2{2, 17}
+         : (P == 8 && Q2 == 2)  ? Ld2{3, 26}
          : (P == 8 && Q2 == 1)  ? Ld2{1, 9}
-         : (P == 4 && Q2 == 2)  ? Ld2{3, 13}
+         : (P == 4 && Q2 == 2)  ? Ld2{3, 14}
                                 : Ld2{1, 5};  // P = 4, Q2 = 1
 }
 }  // namespace bank
@@ -251,10 +253,21 @@ struct Plan {
   // words (both IFs) in shared memory; otherwise (small N) every lane loads its own words
   static constexpr int TILE1 = WARPS * CW;
   static constexpr bool STAGED1 = (N2 % TILE1 == 0) && (TILE1 % 32 == 0);
+  // staged row: the tile's words of the two IFs interleaved (word w of IF a, of IF b, ...)
+  // so that one 8-byte load fetches both, plus two pad words (rows of distinct q1 then fall
+  // on distinct bank pairs)
   template <int BITS>
-  static constexpr int stage_row() { return 2 * (TILE1 * BITS / 32) + 1; }  // both IFs + 1 pad word
+  static constexpr int stage_row() { return 2 * (TILE1 * BITS / 32) + 2; }
+  // stage buffers: two (the next tile in flight) where two CTAs per SM still fit, else one
+  static constexpr size_t kSmemPerCta2 = (233472 - 2 * 1024) / 2;
   template <int BITS>
-  static constexpr int stage_words() { return STAGED1 ? 2 * N1 * stage_row<BITS>() : 0; }  // 2 buffers
+  static constexpr int stage_bufs() {
+    return (sizeof(float2) * (size_t)WARPS * REGION1 + 4 * (size_t)2 * N1 * stage_row<BITS>() + 16 <= kSmemPerCta2)
+               ? 2
+               : 1;
+  }
+  template <int BITS>
+  static constexpr int stage_words() { return STAGED1 ? stage_bufs<BITS>() * N1 * stage_row<BITS>() : 0; }
   template <int BITS>
   static constexpr size_t smem1() {
     return sizeof(float2) * (size_t)WARPS * REGION1 + 4 * (size_t)stage_words<BITS>() + 16;
@@ -268,7 +281,9 @@ struct Plan {
   static constexpr bank::Ld2 L2 = bank::p2_layout(P, Q2);
   static constexpr int LDQ2 = L2.a, LDE2 = L2.b;
   static constexpr int REGION2 = (2 * UPW * LDE2 > 2 * UPW * N2) ? 2 * UPW * LDE2 : 2 * UPW * N2;
-  static constexpr int TWT = N2 + N2 / 32 + 1;             // skewed W_N2 table (index k + k/32)
+  // W_N2^k at k + k/32.  (A lane-contiguous [q][p] table has fewer bank conflicts but
+  // measured slower in this kernel.)
+  static constexpr int TWT = N2 + N2 / 32 + 1;
   static constexpr int TACC = ((2 * P + 15) / 16) * 16;    // tensor-memory columns per lane: accumulators
   static constexpr int TTW = ((2 * P + 15) / 16) * 16;     // and the lane's column twiddles W_N^{b u}
   static constexpr int TCOLS2 = pow2_at_least((WARPS / 4) * (TACC + TTW), 32);

@@ -19,6 +19,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "polaris_device.cuh"
 
 namespace polaris {
@@ -81,6 +84,16 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// TMA store of a 2-D box (x = column, y = row) from shared memory; one bulk group per call
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];\n" ::"l"(map),
+               "r"(smem_addr(src)), "r"(x), "r"(y)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------------------------------
 // tensor memory (TMEM) as per-thread storage: warp w reaches lanes 32 (w % 4) .. +31; a
@@ -200,13 +213,17 @@ __device__ __forceinline__ void cta_tmem_end(uint32_t tbase, int warp) {
 // the N1-point DFT with Q1-point register DFTs.  Output slab layout: [pair-segment][c][b].
 // ------------------------------------------------------------------------------------------
 template <int LOGN, int BITS>
-__global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase1(BatchArgs a) {
+__global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2)
+    k_phase1(BatchArgs a, const __grid_constant__ CUtensorMap slab_map) {
   using PL = Plan<LOGN>;
   constexpr int P = PL::P, N1 = PL::N1, N2 = PL::N2, Q1 = PL::Q1, CW = PL::CW, PQ = PL::PQ;
   constexpr int LDP = PL::LDP1, LDQ = PL::LDQ1;
   constexpr bool STAGED = PL::STAGED1;
   constexpr int TILE = PL::TILE1, WPR = STAGED ? TILE * BITS / 32 : 1;  // words per row of a tile
-  extern __shared__ float2 sm1[];
+  constexpr bool TMA_OUT = STAGED;  // the warp's [N1][CW] output block leaves by one TMA store
+  static_assert(!TMA_OUT || (Q1 > 1 && N1 <= 256 && N1 * CW <= PL::REGION1 && (PL::REGION1 * 8) % 128 == 0),
+                "TMA output tile");
+  extern __shared__ __align__(128) float2 sm1[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int q1 = lane / CW, cw = lane % CW;
   float2* region = sm1 + warp * PL::REGION1;
@@ -232,8 +249,10 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase1(BatchArgs a) 
     tmem_wait_st();
   }
 
-  // the second half of the work on one column group: twiddle, transpose, Q1-point DFTs, store
-  auto finish = [&](float2 (&v)[P], bool act, long long g, long long b) {
+  // the second half of the work on one column group: twiddle, transpose, Q1-point DFTs, store.
+  // After the transpose lane (q1, cw) holds, for p = r Q1 + q1, the Q1 values of row p; its
+  // DFT gives rows c = p + P m of the slab.
+  auto finish = [&](float2 (&v)[P], bool act, long long g, long long b, int xcol) {
     dit<P>(v);
     if constexpr (Q1 > 1) {
       sfor<0, P / 8>([&](auto c_) {
@@ -247,29 +266,56 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase1(BatchArgs a) 
           if constexpr (p > 0) v[p] = cmul(v[p], make_float2(w16[2 * k], w16[2 * k + 1]));
         });
       });
+      if constexpr (TMA_OUT) {
+        if (lane == 0) bulk_wait_read();  // the previous output tile has left the region
+        __syncwarp();
+      }
       sfor<0, P>([&](auto p_) {
         constexpr int p = decltype(p_)::value;
         region[q1 * LDQ + p * LDP + cw] = v[p];
       });
       __syncwarp();
-      sfor<0, PQ>([&](auto r_) {
-        constexpr int r = decltype(r_)::value;
-        const int p = q1 * PQ + r;
-        float2 u[Q1];
-        sfor<0, Q1>([&](auto q_) {
-          constexpr int q = decltype(q_)::value;
-          u[ct::bitrev(q, Q1)] = region[q * LDQ + p * LDP + cw];
+      if constexpr (TMA_OUT) {
+        sfor<0, PQ>([&](auto r_) {
+          constexpr int r = decltype(r_)::value;
+          const int p = r * Q1 + q1;
+          sfor<0, Q1>([&](auto q_) {
+            constexpr int q = decltype(q_)::value;
+            v[r * Q1 + ct::bitrev(q, Q1)] = region[q * LDQ + p * LDP + cw];
+          });
         });
-        dit<Q1>(u);
-        if (act) {
-          float2* dst = a.scratch + ((size_t)g * N1 + p) * N2 + b;
+        __syncwarp();  // region consumed: it now takes the output tile [c][cw]
+        sfor<0, PQ>([&](auto r_) {
+          constexpr int r = decltype(r_)::value;
+          dit<Q1, r * Q1, 1>(v);
           sfor<0, Q1>([&](auto m_) {
             constexpr int m = decltype(m_)::value;
-            dst[(size_t)m * P * N2] = u[m];
+            region[(r * Q1 + q1 + P * m) * CW + cw] = v[r * Q1 + m];
           });
-        }
-      });
-      __syncwarp();  // region free for the next item
+        });
+        fence_async_shared();
+        __syncwarp();
+        if (lane == 0 && act) tma_store_2d(&slab_map, region, xcol, (int)(g * N1));
+      } else {
+        sfor<0, PQ>([&](auto r_) {
+          constexpr int r = decltype(r_)::value;
+          const int p = r * Q1 + q1;
+          float2 u[Q1];
+          sfor<0, Q1>([&](auto q_) {
+            constexpr int q = decltype(q_)::value;
+            u[ct::bitrev(q, Q1)] = region[q * LDQ + p * LDP + cw];
+          });
+          dit<Q1>(u);
+          if (act) {
+            float2* dst = a.scratch + ((size_t)g * N1 + p) * N2 + b;
+            sfor<0, Q1>([&](auto m_) {
+              constexpr int m = decltype(m_)::value;
+              dst[(size_t)m * P * N2] = u[m];
+            });
+          }
+        });
+        __syncwarp();  // region free for the next item
+      }
     } else {
       if (act) {
         float2* dst = a.scratch + (size_t)g * N1 * N2 + b;
@@ -296,15 +342,16 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase1(BatchArgs a) 
       } else {
         sfor<0, P>([&](auto t_) { v[decltype(t_)::value] = make_float2(0.f, 0.f); });
       }
-      finish(v, act, g, b);
+      finish(v, act, g, b, 0);
     }
   } else {
     // CTA tiles of TILE columns of one pair-segment.  The packed words of a tile (both IFs)
     // are staged in shared memory with cp.async, double-buffered so that the next tile's
     // words are in flight while the warps work on this one; every warp decodes its CW
     // columns from the stage.
-    constexpr int RS = PL::template stage_row<BITS>();  // words per staged row (odd: no conflicts)
-    constexpr int SB = N1 * RS;                         // words per stage buffer
+    constexpr int RS = PL::template stage_row<BITS>();   // words per staged row
+    constexpr int SB = N1 * RS;                          // words per stage buffer
+    constexpr int NB = PL::template stage_bufs<BITS>();  // 2: next tile in flight
     const long long n_tiles = total_cols / TILE;
     const uint32_t stage_a = smem_addr(stage);
     auto issue = [&](long long tile, int buf) {
@@ -319,17 +366,20 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase1(BatchArgs a) 
       for (int k = threadIdx.x; k < N1 * WPR; k += PL::THREADS) {
         const int row = k / WPR, wd = k % WPR;
         const size_t off = (size_t)row * (N2 * BITS / 32) + wd;
-        cp_async4(dst0 + 4u * (uint32_t)(row * RS + wd), pa + off);
-        if (pb) cp_async4(dst0 + 4u * (uint32_t)(row * RS + WPR + wd), pb + off);
+        cp_async4(dst0 + 4u * (uint32_t)(row * RS + 2 * wd), pa + off);
+        if (pb) cp_async4(dst0 + 4u * (uint32_t)(row * RS + 2 * wd + 1), pb + off);
       }
       cp_async_commit();
     };
     long long tile = blockIdx.x;
     if (tile < n_tiles) issue(tile, 0);
-    for (int buf = 0; tile < n_tiles; tile += gridDim.x, buf ^= 1) {
+    for (int buf = 0; tile < n_tiles; tile += gridDim.x, buf = (NB == 2) ? buf ^ 1 : 0) {
       cp_async_wait_all();
       __syncthreads();  // this tile's words are staged; every warp is done with the other buffer
-      if (tile + gridDim.x < n_tiles) issue(tile + gridDim.x, buf ^ 1);
+      const long long next = tile + gridDim.x;
+      if constexpr (NB == 2) {
+        if (next < n_tiles) issue(next, buf ^ 1);
+      }
       const long long gc0 = tile * TILE;
       const int g = (int)(gc0 / N2), b0 = (int)(gc0 % N2);
       const int f = g % a.n_fpair;
@@ -338,14 +388,15 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase1(BatchArgs a) 
       const long long b = b0 + col;
       const int wd = (col * BITS) >> 5;
       const uint32_t shift = (uint32_t)((col * BITS) & 31);
-      const uint32_t* sb = stage + buf * SB;
+      const uint32_t* sb = stage + buf * SB + 2 * wd;
       const float* taps = a.taps;
       float2 v[P];
       sfor<0, P>([&](auto t_) {
         constexpr int t = decltype(t_)::value;
         const int row = q1 + Q1 * t;
-        float x = decode_level<BITS>(sb[row * RS + wd], shift);
-        float y = has_b ? decode_level<BITS>(sb[row * RS + WPR + wd], shift) : 0.0f;
+        const uint2 w = *reinterpret_cast<const uint2*>(sb + row * RS);  // IF a, IF b
+        float x = decode_level<BITS>(w.x, shift);
+        float y = has_b ? decode_level<BITS>(w.y, shift) : 0.0f;
         if (taps) {
           const float tv = __ldg(taps + row * N2 + b);
           x *= tv;
@@ -353,9 +404,16 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase1(BatchArgs a) 
         }
         v[ct::bitrev(t, P)] = make_float2(x, y);
       });
-      finish(v, true, g, b);
+      if constexpr (NB == 1) {
+        __syncthreads();  // every warp has decoded: the single buffer is free
+        if (next < n_tiles) issue(next, 0);
+      }
+      finish(v, true, g, b, b0 + warp * CW);
     }
     cp_async_wait_all();
+  }
+  if constexpr (TMA_OUT) {
+    if (lane == 0) bulk_wait_all();  // output tiles written before the CTA's shared memory goes
   }
   if constexpr (Q1 > 1) cta_tmem_end<PL::TCOLS1>(tbase, warp);
 }
@@ -623,6 +681,28 @@ static int ctas_per_sm(K kernel, int threads, size_t smem) {
   return n < 1 ? 1 : n;
 }
 
+// Tensor map over the slab of one batch, rows (pair-segment, c) x columns b of 8-byte
+// complex values; box = one warp's output block (CW columns x N1 rows).
+static cudaError_t encode_slab_map(CUtensorMap* map, float2* slab, long long rows, int n2, int cw, int n1) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)n2, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)n2 * sizeof(float2)};
+  const cuuint32_t box[2] = {(cuuint32_t)cw, (cuuint32_t)n1};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, slab, dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int LOGN, int BITS>
 static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st) {
   using PL = Plan<LOGN>;
@@ -636,10 +716,17 @@ static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st) {
     per_sm = ctas_per_sm(k_phase1<LOGN, BITS>, PL::THREADS, PL::template smem1<BITS>());
     attr_dev = dev;
   }
+  alignas(64) CUtensorMap map;
+  memset(&map, 0, sizeof map);
+  if constexpr (PL::STAGED1) {
+    if ((reinterpret_cast<uintptr_t>(a.scratch) & 15) != 0) return cudaErrorMisalignedAddress;
+    const cudaError_t e = encode_slab_map(&map, a.scratch, (long long)a.nseg * a.n_fpair * PL::N1, PL::N2, PL::CW, PL::N1);
+    if (e != cudaSuccess) return e;
+  }
   const long long items = ((long long)a.nseg * a.n_fpair * PL::N2 + PL::CW - 1) / PL::CW;
   const long long ctas = (items + PL::WARPS - 1) / PL::WARPS;  // = tiles when staged
   const long long cap = (long long)per_sm * a.num_sms;
-  k_phase1<LOGN, BITS><<<(int)(ctas < cap ? ctas : cap), PL::THREADS, PL::template smem1<BITS>(), st>>>(a);
+  k_phase1<LOGN, BITS><<<(int)(ctas < cap ? ctas : cap), PL::THREADS, PL::template smem1<BITS>(), st>>>(a, map);
   return cudaGetLastError();
 }
 
