@@ -87,37 +87,33 @@ struct ReadoutArgs {
 // the accumulators start the next integration at zero without a separate memset.
 constexpr int kReadoutMinTile = 512;  // natural bins per block (at least N1; TD >= 2 at N1 <= 256)
 constexpr int kReadoutThreads = 256;
-constexpr int kReadoutPerThread = 4;  // covers N1 <= 1024
 
+template <int LN1>
 __global__ void __launch_bounds__(kReadoutThreads) k_readout(ReadoutArgs a) {
-  __shared__ float4 tile[1024 + 128];  // TD (N1 + 1) <= TE + TD entries; TE <= 1024, TD <= 128
-  const int f = blockIdx.y, N1 = a.N1, N2 = a.N2;
-  const int TD = N1 >= kReadoutMinTile ? 1 : kReadoutMinTile / N1, TE = TD * N1;
+  constexpr int N1 = 1 << LN1;
+  constexpr int TD = N1 >= kReadoutMinTile ? 1 : kReadoutMinTile / N1, TE = TD * N1;
+  constexpr int PT = (TE + kReadoutThreads - 1) / kReadoutThreads;  // entries per thread
+  __shared__ float4 tile[TD * (N1 + 1)];
+  const int f = blockIdx.y, N2 = a.N2;
   const int d0 = blockIdx.x * TD;
   const size_t fo = (size_t)f * a.native;
-  int slot[kReadoutPerThread], sidx[kReadoutPerThread];
-  bool cjv[kReadoutPerThread];
-  float4 v[kReadoutPerThread];
+  int slot[PT], sidx[PT];
+  float4 v[PT];
   // all loads first (several in flight per thread), then the clears and the shared stores
 #pragma unroll
-  for (int i = 0; i < kReadoutPerThread; ++i) {
+  for (int i = 0; i < PT; ++i) {
     const int e = threadIdx.x + i * kReadoutThreads;
     slot[i] = -1;
-    const int c = e / TD, dd = e - c * TD, d = d0 + dd;
+    const int c = e / TD, dd = e % TD, d = d0 + dd;
     const int k = c + N1 * d;
     if (e >= TE || k >= a.nbin) continue;
     int idx;
-    bool cj = false;
     if (c == 0) idx = d;
     else if (c == N1 / 2) idx = (d <= N2 / 2 - 2) ? N2 / 2 + 1 + d : a.UPS * N2;
     else if (c < N1 / 2) idx = c * N2 + d;
-    else {
-      idx = (N1 - c) * N2 + (N2 - 1 - d);
-      cj = true;
-    }
+    else idx = (N1 - c) * N2 + (N2 - 1 - d);
     slot[i] = idx;
     sidx[i] = dd * (N1 + 1) + c;
-    cjv[i] = cj;
     if (a.fp64) {
       const double4 w = reinterpret_cast<const double4*>(a.acc)[fo + idx];
       v[i] = make_float4((float)(0.25 * w.x), (float)(0.25 * w.y), (float)(0.25 * w.z), (float)(0.25 * w.w));
@@ -125,15 +121,14 @@ __global__ void __launch_bounds__(kReadoutThreads) k_readout(ReadoutArgs a) {
       const float4 w = reinterpret_cast<const float4*>(a.acc)[fo + idx];
       v[i] = make_float4(0.25f * w.x, 0.25f * w.y, 0.25f * w.z, 0.25f * w.w);
     }
+    if (c > N1 / 2) v[i].w = -v[i].w;  // mirror column: conjugate
   }
 #pragma unroll
-  for (int i = 0; i < kReadoutPerThread; ++i) {
+  for (int i = 0; i < PT; ++i) {
     if (slot[i] < 0) continue;
     if (a.fp64) reinterpret_cast<double4*>(a.acc)[fo + slot[i]] = make_double4(0.0, 0.0, 0.0, 0.0);
     else reinterpret_cast<float4*>(a.acc)[fo + slot[i]] = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 t = v[i];
-    if (cjv[i]) t.w = -t.w;
-    tile[sidx[i]] = t;
+    tile[sidx[i]] = v[i];
   }
   __syncthreads();
   const int p = a.fcorr[f];
@@ -184,6 +179,21 @@ __global__ void __launch_bounds__(kReadoutThreads) k_readout(ReadoutArgs a) {
 static dim3 readout_grid(int N1, int N2, int n_fpair) {
   const int td = N1 >= kReadoutMinTile ? 1 : kReadoutMinTile / N1;
   return dim3((unsigned)((N2 / 2 + 1 + td - 1) / td), (unsigned)n_fpair);
+}
+
+static cudaError_t launch_readout(const ReadoutArgs& r, int n_fpair, cudaStream_t st) {
+  const dim3 grid = readout_grid(r.N1, r.N2, n_fpair);
+  switch (r.N1) {
+#define POLARIS_RO(LN1)                                        \
+  case 1 << LN1:                                               \
+    k_readout<LN1><<<grid, kReadoutThreads, 0, st>>>(r);        \
+    break;
+    POLARIS_RO(1) POLARIS_RO(2) POLARIS_RO(3) POLARIS_RO(4) POLARIS_RO(5) POLARIS_RO(6) POLARIS_RO(7)
+    POLARIS_RO(8) POLARIS_RO(9) POLARIS_RO(10)
+#undef POLARIS_RO
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 static int host_plan_n2(int logn) { return 1 << plan_log_n2(logn); }
@@ -709,11 +719,7 @@ extern "C" int spectrometer_integrate_device(polaris_spec* s, const polaris_stok
   r.autos = d_autos;
   r.cross = d_cross;
   r.stokes = d_stokes;
-  const dim3 grid = readout_grid(s->N1, s->N2, s->n_fpair);
-  CUDA_OR_FAIL(s, counted_launch(s, 2, st, [&]() {
-                  k_readout<<<grid, kReadoutThreads, 0, st>>>(r);
-                  return cudaGetLastError();
-                }));
+  CUDA_OR_FAIL(s, counted_launch(s, 2, st, [&]() { return launch_readout(r, s->n_fpair, st); }));
   // (the readout has cleared the accumulators it read)
   if (n_segments_out) *n_segments_out = s->seg_acc;
   s->seg_acc = 0;
@@ -1027,8 +1033,7 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
   r.autos = d_autos;
   r.cross = n_pair ? d_cross : nullptr;
   r.stokes = n_pair ? d_stokes : nullptr;
-  k_readout<<<readout_grid(r.N1, r.N2, nf), kReadoutThreads, 0, st>>>(r);
-  e = cudaGetLastError();
+  e = launch_readout(r, nf, st);
   if (e != cudaSuccess) return set_err(nullptr, POLARIS_ECUDA, "no-alloc readout: %s", cudaGetErrorString(e));
   if (n_segments_out) *n_segments_out = nseg;
   return POLARIS_OK;

@@ -20,6 +20,7 @@
 #include <cuda_runtime.h>
 
 #include <cuda.h>
+#include <type_traits>
 #include <cudaTypedefs.h>
 
 #include "polaris_device.cuh"
@@ -84,13 +85,18 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-// TMA store of a 2-D box (x = column, y = row) from shared memory; one bulk group per call
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];\n" ::"l"(map),
-               "r"(smem_addr(src)), "r"(x), "r"(y)
-               : "memory");
-  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+// TMA store of a 2-D box (x = column, y = row) from shared memory, issued by one elected lane
+// of the (converged) warp as one bulk group; predicated, so the warp never branches apart
+__device__ __forceinline__ void tma_store_2d_elect(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile(
+      "{\n .reg .pred p;\n .reg .b32 r;\n elect.sync r|p, 0xffffffff;\n"
+      " @p cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];\n"
+      " @p cp.async.bulk.commit_group;\n}\n" ::"l"(map),
+      "r"(smem_addr(src)), "r"(x), "r"(y)
+      : "memory");
 }
+// wait until this thread's bulk groups have finished reading shared memory (a lane that
+// issued none returns at once)
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
@@ -267,7 +273,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2)
         });
       });
       if constexpr (TMA_OUT) {
-        if (lane == 0) bulk_wait_read();  // the previous output tile has left the region
+        bulk_wait_read();  // the previous output tile has left the region
         __syncwarp();
       }
       sfor<0, P>([&](auto p_) {
@@ -295,7 +301,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2)
         });
         fence_async_shared();
         __syncwarp();
-        if (lane == 0 && act) tma_store_2d(&slab_map, region, xcol, (int)(g * N1));
+        if (act) tma_store_2d_elect(&slab_map, region, xcol, (int)(g * N1));
       } else {
         sfor<0, PQ>([&](auto r_) {
           constexpr int r = decltype(r_)::value;
@@ -354,21 +360,32 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2)
     constexpr int NB = PL::template stage_bufs<BITS>();  // 2: next tile in flight
     const long long n_tiles = total_cols / TILE;
     const uint32_t stage_a = smem_addr(stage);
+    // this thread's share of a tile's words: source offsets (words from the tile's first word
+    // of its row 0) and stage offsets (bytes), the same for every tile
+    constexpr int KW = N1 * WPR, KPT = (KW + PL::THREADS - 1) / PL::THREADS;
+    uint32_t soff[KPT], doff[KPT];
+    sfor<0, KPT>([&](auto i_) {
+      constexpr int i = decltype(i_)::value;
+      const int k = (int)threadIdx.x + i * PL::THREADS;
+      const int row = k / WPR, wd = k % WPR;
+      soff[i] = (uint32_t)(row * (N2 * BITS / 32) + wd);
+      doff[i] = 4u * (uint32_t)(row * RS + 2 * wd);
+    });
     auto issue = [&](long long tile, int buf) {
-      const long long gc0 = tile * TILE;
-      const int g = (int)(gc0 / N2), b0 = (int)(gc0 % N2);
+      const int g = (int)(tile / (N2 / TILE)), b0 = (int)(tile % (N2 / TILE)) * TILE;
       const int s_local = g / a.n_fpair, f = g - s_local * a.n_fpair;
       const int sg = a.seg0 + s_local;
       const int ia = a.fa[f], ib = a.fb[f];
       const uint32_t* pa = seg_ptr(a.in, ia, sg) + (b0 * BITS) / 32;
-      const uint32_t* pb = ib >= 0 ? seg_ptr(a.in, ib, sg) + (b0 * BITS) / 32 : nullptr;
+      const uint32_t* pb = ib >= 0 ? seg_ptr(a.in, ib, sg) + (b0 * BITS) / 32 : pa;
       const uint32_t dst0 = stage_a + 4u * (uint32_t)(buf * SB);
-      for (int k = threadIdx.x; k < N1 * WPR; k += PL::THREADS) {
-        const int row = k / WPR, wd = k % WPR;
-        const size_t off = (size_t)row * (N2 * BITS / 32) + wd;
-        cp_async4(dst0 + 4u * (uint32_t)(row * RS + 2 * wd), pa + off);
-        if (pb) cp_async4(dst0 + 4u * (uint32_t)(row * RS + 2 * wd + 1), pb + off);
-      }
+      sfor<0, KPT>([&](auto i_) {
+        constexpr int i = decltype(i_)::value;
+        if (KW % PL::THREADS == 0 || (int)threadIdx.x + i * PL::THREADS < KW) {
+          cp_async4(dst0 + doff[i], pa + soff[i]);
+          cp_async4(dst0 + doff[i] + 4u, pb + soff[i]);  // (IF a again when the pair has no IF b)
+        }
+      });
       cp_async_commit();
     };
     long long tile = blockIdx.x;
@@ -380,8 +397,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2)
       if constexpr (NB == 2) {
         if (next < n_tiles) issue(next, buf ^ 1);
       }
-      const long long gc0 = tile * TILE;
-      const int g = (int)(gc0 / N2), b0 = (int)(gc0 % N2);
+      const int g = (int)(tile / (N2 / TILE)), b0 = (int)(tile % (N2 / TILE)) * TILE;
       const int f = g % a.n_fpair;
       const bool has_b = a.fb[f] >= 0;
       const int col = warp * CW + cw;  // column inside the tile
@@ -389,21 +405,33 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2)
       const int wd = (col * BITS) >> 5;
       const uint32_t shift = (uint32_t)((col * BITS) & 31);
       const uint32_t* sb = stage + buf * SB + 2 * wd;
-      const float* taps = a.taps;
       float2 v[P];
-      sfor<0, P>([&](auto t_) {
-        constexpr int t = decltype(t_)::value;
-        const int row = q1 + Q1 * t;
-        const uint2 w = *reinterpret_cast<const uint2*>(sb + row * RS);  // IF a, IF b
-        float x = decode_level<BITS>(w.x, shift);
-        float y = has_b ? decode_level<BITS>(w.y, shift) : 0.0f;
-        if (taps) {
-          const float tv = __ldg(taps + row * N2 + b);
-          x *= tv;
-          y *= tv;
-        }
-        v[ct::bitrev(t, P)] = make_float2(x, y);
-      });
+      // decode the lane's 32 rows; the pair's shape and the window are uniform per tile
+      auto decode = [&](auto hb_, auto tp_) {
+        constexpr bool HB = decltype(hb_)::value, TP = decltype(tp_)::value;
+        sfor<0, P>([&](auto t_) {
+          constexpr int t = decltype(t_)::value;
+          const int row = q1 + Q1 * t;
+          const uint2 w = *reinterpret_cast<const uint2*>(sb + row * RS);  // IF a, IF b
+          float x = decode_level<BITS>(w.x, shift);
+          float y = HB ? decode_level<BITS>(w.y, shift) : 0.0f;
+          if constexpr (TP) {
+            const float tv = __ldg(a.taps + row * N2 + b);
+            x *= tv;
+            y *= tv;
+          }
+          v[ct::bitrev(t, P)] = make_float2(x, y);
+        });
+      };
+      using T_ = std::true_type;
+      using F_ = std::false_type;
+      if (a.taps) {
+        if (has_b) decode(T_{}, T_{});
+        else decode(F_{}, T_{});
+      } else {
+        if (has_b) decode(T_{}, F_{});
+        else decode(F_{}, F_{});
+      }
       if constexpr (NB == 1) {
         __syncthreads();  // every warp has decoded: the single buffer is free
         if (next < n_tiles) issue(next, 0);
@@ -413,7 +441,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2)
     cp_async_wait_all();
   }
   if constexpr (TMA_OUT) {
-    if (lane == 0) bulk_wait_all();  // output tiles written before the CTA's shared memory goes
+    bulk_wait_all();  // output tiles written before the CTA's shared memory goes
   }
   if constexpr (Q1 > 1) cta_tmem_end<PL::TCOLS1>(tbase, warp);
 }
