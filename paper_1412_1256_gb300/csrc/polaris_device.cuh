@@ -249,9 +249,12 @@ struct Plan {
   static constexpr int REGION1 = Q1 > 1 ? Q1 * LDQ1 : 0;  // float2 per warp
   static constexpr int TW1 = ((2 * P + 15) / 16) * 16;      // tensor-memory columns per lane (W_N1 twiddles)
   static constexpr int TCOLS1 = pow2_at_least((WARPS / 4) * TW1, 32);
-  // CTA tiles of WARPS * CW columns inside one segment: the CTA stages the tile's packed
-  // words (both IFs) in shared memory; otherwise (small N) every lane loads its own words
-  static constexpr int TILE1 = WARPS * CW;
+  // CTA tiles of IPT1 * WARPS * CW columns inside one segment: the CTA stages the tile's
+  // packed words (both IFs) in shared memory; otherwise (small N) every lane loads its own
+  // words.  IPT1 column groups per warp per tile: two where such a tile still divides N2
+  // (halves the CTA barriers and the per-tile staging work per column).
+  static constexpr int IPT1 = (N2 % (2 * WARPS * CW) == 0) ? 2 : 1;
+  static constexpr int TILE1 = IPT1 * WARPS * CW;
   static constexpr bool STAGED1 = (N2 % TILE1 == 0) && (TILE1 % 32 == 0);
   // staged row: the tile's words of the two IFs interleaved (word w of IF a, of IF b, ...)
   // so that one 8-byte load fetches both, plus two pad words (rows of distinct q1 then fall

@@ -225,8 +225,9 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2)
   constexpr int P = PL::P, N1 = PL::N1, N2 = PL::N2, Q1 = PL::Q1, CW = PL::CW, PQ = PL::PQ;
   constexpr int LDP = PL::LDP1, LDQ = PL::LDQ1;
   constexpr bool STAGED = PL::STAGED1;
-  constexpr int TILE = PL::TILE1, WPR = STAGED ? TILE * BITS / 32 : 1;  // words per row of a tile
-  constexpr bool TMA_OUT = STAGED;  // the warp's [N1][CW] output block leaves by one TMA store
+  constexpr int TILE = PL::TILE1, IPT = PL::IPT1, WPR = STAGED ? TILE * BITS / 32 : 1;  // words per tile row
+  // the warp's [N1][CW] output block leaves by one TMA store (a box is at most 256 rows)
+  constexpr bool TMA_OUT = STAGED && N1 <= 256;
   static_assert(!TMA_OUT || (Q1 > 1 && N1 <= 256 && N1 * CW <= PL::REGION1 && (PL::REGION1 * 8) % 128 == 0),
                 "TMA output tile");
   extern __shared__ __align__(128) float2 sm1[];
@@ -400,43 +401,47 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2)
       const int g = (int)(tile / (N2 / TILE)), b0 = (int)(tile % (N2 / TILE)) * TILE;
       const int f = g % a.n_fpair;
       const bool has_b = a.fb[f] >= 0;
-      const int col = warp * CW + cw;  // column inside the tile
-      const long long b = b0 + col;
-      const int wd = (col * BITS) >> 5;
-      const uint32_t shift = (uint32_t)((col * BITS) & 31);
-      const uint32_t* sb = stage + buf * SB + 2 * wd;
-      float2 v[P];
-      // decode the lane's 32 rows; the pair's shape and the window are uniform per tile
-      auto decode = [&](auto hb_, auto tp_) {
-        constexpr bool HB = decltype(hb_)::value, TP = decltype(tp_)::value;
-        sfor<0, P>([&](auto t_) {
-          constexpr int t = decltype(t_)::value;
-          const int row = q1 + Q1 * t;
-          const uint2 w = *reinterpret_cast<const uint2*>(sb + row * RS);  // IF a, IF b
-          float x = decode_level<BITS>(w.x, shift);
-          float y = HB ? decode_level<BITS>(w.y, shift) : 0.0f;
-          if constexpr (TP) {
-            const float tv = __ldg(a.taps + row * N2 + b);
-            x *= tv;
-            y *= tv;
-          }
-          v[ct::bitrev(t, P)] = make_float2(x, y);
-        });
-      };
-      using T_ = std::true_type;
-      using F_ = std::false_type;
-      if (a.taps) {
-        if (has_b) decode(T_{}, T_{});
-        else decode(F_{}, T_{});
-      } else {
-        if (has_b) decode(T_{}, F_{});
-        else decode(F_{}, F_{});
-      }
-      if constexpr (NB == 1) {
-        __syncthreads();  // every warp has decoded: the single buffer is free
-        if (next < n_tiles) issue(next, 0);
-      }
-      finish(v, true, g, b, b0 + warp * CW);
+      // IPT column groups per warp per tile: group it of warp w holds columns (it WARPS + w) CW + cw
+      sfor<0, IPT>([&](auto it_) {
+        constexpr int it = decltype(it_)::value;
+        const int col = (it * PL::WARPS + warp) * CW + cw;  // column inside the tile
+        const long long b = b0 + col;
+        const int wd = (col * BITS) >> 5;
+        const uint32_t shift = (uint32_t)((col * BITS) & 31);
+        const uint32_t* sb = stage + buf * SB + 2 * wd;
+        float2 v[P];
+        // decode the lane's 32 rows; the pair's shape and the window are uniform per tile
+        auto decode = [&](auto hb_, auto tp_) {
+          constexpr bool HB = decltype(hb_)::value, TP = decltype(tp_)::value;
+          sfor<0, P>([&](auto t_) {
+            constexpr int t = decltype(t_)::value;
+            const int row = q1 + Q1 * t;
+            const uint2 w = *reinterpret_cast<const uint2*>(sb + row * RS);  // IF a, IF b
+            float x = decode_level<BITS>(w.x, shift);
+            float y = HB ? decode_level<BITS>(w.y, shift) : 0.0f;
+            if constexpr (TP) {
+              const float tv = __ldg(a.taps + row * N2 + b);
+              x *= tv;
+              y *= tv;
+            }
+            v[ct::bitrev(t, P)] = make_float2(x, y);
+          });
+        };
+        using T_ = std::true_type;
+        using F_ = std::false_type;
+        if (a.taps) {
+          if (has_b) decode(T_{}, T_{});
+          else decode(F_{}, T_{});
+        } else {
+          if (has_b) decode(T_{}, F_{});
+          else decode(F_{}, F_{});
+        }
+        if constexpr (NB == 1 && it == IPT - 1) {
+          __syncthreads();  // every warp has decoded the tile: the single buffer is free
+          if (next < n_tiles) issue(next, 0);
+        }
+        finish(v, true, g, b, b0 + (it * PL::WARPS + warp) * CW);
+      });
     }
     cp_async_wait_all();
   }
@@ -746,13 +751,14 @@ static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st) {
   }
   alignas(64) CUtensorMap map;
   memset(&map, 0, sizeof map);
-  if constexpr (PL::STAGED1) {
+  if constexpr (PL::STAGED1 && PL::N1 <= 256) {  // the kernel's TMA output path
     if ((reinterpret_cast<uintptr_t>(a.scratch) & 15) != 0) return cudaErrorMisalignedAddress;
     const cudaError_t e = encode_slab_map(&map, a.scratch, (long long)a.nseg * a.n_fpair * PL::N1, PL::N2, PL::CW, PL::N1);
     if (e != cudaSuccess) return e;
   }
-  const long long items = ((long long)a.nseg * a.n_fpair * PL::N2 + PL::CW - 1) / PL::CW;
-  const long long ctas = (items + PL::WARPS - 1) / PL::WARPS;  // = tiles when staged
+  const long long cols = (long long)a.nseg * a.n_fpair * PL::N2;
+  const long long ctas = PL::STAGED1 ? cols / PL::TILE1  // one tile per CTA pass
+                                     : ((cols + PL::CW - 1) / PL::CW + PL::WARPS - 1) / PL::WARPS;
   const long long cap = (long long)per_sm * a.num_sms;
   k_phase1<LOGN, BITS><<<(int)(ctas < cap ? ctas : cap), PL::THREADS, PL::template smem1<BITS>(), st>>>(a, map);
   return cudaGetLastError();
