@@ -179,6 +179,11 @@ __device__ __forceinline__ float decode_level(uint32_t word, uint32_t shift) {
 // ----------------------------------------------------------------------------------------
 // (P, N2) per size; N1 = N / N2.  P = points per thread, 2 <= 2 Q2 <= P, Q1 <= P.
 constexpr int plan_p(int logn) { return logn >= 10 ? 32 : (logn >= 8 ? 16 : (logn >= 6 ? 8 : 4)); }
+// phase-1 points per lane: 16 at N1 = 128 (half the registers of 32, so three CTAs per SM,
+// with the same FFT work per point and warps still four columns = 32 bytes wide).  At
+// N1 = 256 sixteen would leave two-column warps whose 16-byte output rows split sectors;
+// that measured slower than 32 points per lane at two CTAs per SM.
+constexpr int plan_p1(int logn, int n1) { return n1 == 128 ? 16 : plan_p(logn); }
 constexpr int plan_log_n2(int logn) {
   // 4:2 5:3 6:3 7:4 8:4 9:5 10:5 11:6 12:6 13:7 14:7 15:8 16:8 17:9 18:9 19:9
   return logn >= 17 ? 9 : (logn + 1) / 2;
@@ -199,7 +204,10 @@ struct Ld2 {
   int a, b;
 };
 constexpr Ld2 p1_layout(int P, int Q1) {
-  return (P == 32 && Q1 == 2)    ? Ld2{16, 512}
+  return (P == 16 && Q1 == 4)    ? Ld2{8, 136}
+         : (P == 16 && Q1 == 8)  ? Ld2{4, 68}
+         : (P == 16 && Q1 == 16) ? Ld2{2, 34}
+         : (P == 32 && Q1 == 2)  ? Ld2{16, 512}
          : (P == 32 && Q1 == 4)  ? Ld2{8, 264}
          : (P == 32 && Q1 == 8)  ? Ld2{4, 132}
          : (P == 32 && Q1 == 16) ? Ld2{2, 66}
@@ -233,7 +241,8 @@ struct Plan {
   static constexpr int P = plan_p(LOGN);
   static constexpr int N2 = 1 << plan_log_n2(LOGN);
   static constexpr int N1 = N / N2;
-  static constexpr int Q1 = N1 / P;
+  static constexpr int P1 = plan_p1(LOGN, N1);          // phase-1 points per lane
+  static constexpr int Q1 = N1 / P1;
   static constexpr int Q2 = N2 / P;
   static constexpr int UPS = N1 / 2;                   // units (column + mirror) per pair-segment
   static constexpr int NACC = P / 2;                   // accumulator bins per phase-2 lane
@@ -243,38 +252,41 @@ struct Plan {
 
   // phase 1: a warp owns CW columns; lane = q1 * CW + cw holds rows q1 + Q1 t
   static constexpr int CW = 32 / Q1;
-  static constexpr int PQ = P / Q1;
-  static constexpr bank::Ld2 L1 = bank::p1_layout(P, Q1);
+  static constexpr int PQ = P1 / Q1;
+  static constexpr bank::Ld2 L1 = bank::p1_layout(P1, Q1);
   static constexpr int LDP1 = L1.a, LDQ1 = L1.b;
   static constexpr int REGION1 = Q1 > 1 ? Q1 * LDQ1 : 0;  // float2 per warp
-  static constexpr int TW1 = ((2 * P + 15) / 16) * 16;      // tensor-memory columns per lane (W_N1 twiddles)
+  static constexpr int TW1 = ((2 * P1 + 15) / 16) * 16;     // tensor-memory columns per lane (W_N1 twiddles)
+  static constexpr int MINB1 = P1 <= 16 ? 3 : 2;             // phase-1 CTAs per SM the registers aim at
   static constexpr int TCOLS1 = pow2_at_least((WARPS / 4) * TW1, 32);
-  // CTA tiles of IPT1 * WARPS * CW columns inside one segment: the CTA stages the tile's
-  // packed words (both IFs) in shared memory; otherwise (small N) every lane loads its own
-  // words.  IPT1 column groups per warp per tile: two where such a tile still divides N2
-  // (halves the CTA barriers and the per-tile staging work per column).
-  static constexpr int IPT1 = (N2 % (2 * WARPS * CW) == 0) ? 2 : 1;
-  static constexpr int TILE1 = IPT1 * WARPS * CW;
-  static constexpr bool STAGED1 = (N2 % TILE1 == 0) && (TILE1 % 32 == 0);
-  // staged row: the tile's words of the two IFs interleaved (word w of IF a, of IF b, ...)
-  // so that one 8-byte load fetches both, plus two pad words (rows of distinct q1 then fall
-  // on distinct bank pairs)
+  // CTA tiles of IPT * WARPS * CW columns inside one segment (Stage1<BITS>): the CTA stages
+  // the tile's packed words (both IFs) in shared memory; otherwise (small N) every lane loads
+  // its own words.  IPT column groups per warp per tile: two where the tile divides N2 and two
+  // stage buffers still leave room for two CTAs per SM (fewer CTA barriers and less staging
+  // work per column).  Four measured slower at 2^17: too few tiles per SM to balance.
+  static constexpr size_t kSmemPerCta2 = (233472 - MINB1 * 1024) / MINB1;  // MINB1 CTAs per SM
+  static constexpr size_t REGIONS1 = sizeof(float2) * (size_t)WARPS * REGION1;
   template <int BITS>
-  static constexpr int stage_row() { return 2 * (TILE1 * BITS / 32) + 2; }
-  // stage buffers: two (the next tile in flight) where two CTAs per SM still fit, else one
-  static constexpr size_t kSmemPerCta2 = (233472 - 2 * 1024) / 2;
-  template <int BITS>
-  static constexpr int stage_bufs() {
-    return (sizeof(float2) * (size_t)WARPS * REGION1 + 4 * (size_t)2 * N1 * stage_row<BITS>() + 16 <= kSmemPerCta2)
-               ? 2
-               : 1;
-  }
-  template <int BITS>
-  static constexpr int stage_words() { return STAGED1 ? stage_bufs<BITS>() * N1 * stage_row<BITS>() : 0; }
-  template <int BITS>
-  static constexpr size_t smem1() {
-    return sizeof(float2) * (size_t)WARPS * REGION1 + 4 * (size_t)stage_words<BITS>() + 16;
-  }
+  struct Stage1 {
+    // staged row: the tile's words of the two IFs interleaved (word w of IF a, of IF b, ...)
+    // so that one 8-byte load fetches both, plus two pad words (rows of distinct q1 then fall
+    // on distinct bank pairs)
+    static constexpr int row_words(int ipt) { return 2 * (ipt * WARPS * CW * BITS / 32) + 2; }
+    static constexpr bool fits(int ipt, int bufs) {
+      return REGIONS1 + 4 * (size_t)bufs * N1 * row_words(ipt) + 16 <= kSmemPerCta2;
+    }
+    static constexpr bool ok(int ipt) {
+      return N2 % (ipt * WARPS * CW) == 0 && (ipt * WARPS * CW) % 32 == 0 && fits(ipt, 2);
+    }
+    static constexpr int IPT = ok(2) ? 2 : 1;
+    static constexpr int TILE = IPT * WARPS * CW;
+    static constexpr bool STAGED = (N2 % TILE == 0) && (TILE % 32 == 0);
+    static constexpr int WPR = TILE * BITS / 32;  // words per IF per staged row
+    static constexpr int RS = row_words(IPT);
+    static constexpr int NB = fits(IPT, 2) ? 2 : 1;  // 2: the next tile in flight
+    static constexpr int WORDS = STAGED ? NB * N1 * RS : 0;
+    static constexpr size_t SMEM = REGIONS1 + 4 * (size_t)WORDS + 16;
+  };
 
   // phase 2: a warp owns UPW units; lane = (uw * 2 + e) * Q2 + q2 holds rows q2 + Q2 t
   static constexpr int UPW = 16 / Q2;
@@ -293,7 +305,7 @@ struct Plan {
   static constexpr size_t SMEM2 = sizeof(float2) * ((size_t)WARPS * REGION2 + TWT) + 16;
 
   static_assert(N1 * N2 == N, "plan");
-  static_assert(Q1 >= 1 && Q1 <= 32 && P % Q1 == 0 && Q2 >= 1 && 2 * Q2 <= P && 16 % Q2 == 0, "plan bounds");
+  static_assert(Q1 >= 1 && Q1 <= 32 && P1 % Q1 == 0 && Q2 >= 1 && 2 * Q2 <= P && 16 % Q2 == 0, "plan bounds");
   static_assert(N1 <= 1024 && N2 <= 1024, "constant twiddle table covers L <= 1024");
   static_assert(UPS % UPW == 0 || UPW % UPS == 0, "units per warp");
   static_assert(TCOLS1 <= 256 && TCOLS2 <= 256, "tensor memory per CTA");

@@ -147,9 +147,9 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&r)[16]) 
 // phase 1
 // ------------------------------------------------------------------------------------------
 template <int LOGN, int BITS>
-__device__ __forceinline__ void p1_load(const BatchArgs& a, int g, int b, int q1, float2 (&v)[Plan<LOGN>::P]) {
+__device__ __forceinline__ void p1_load(const BatchArgs& a, int g, int b, int q1, float2 (&v)[Plan<LOGN>::P1]) {
   using PL = Plan<LOGN>;
-  constexpr int P = PL::P, N2 = PL::N2, Q1 = PL::Q1;
+  constexpr int P = PL::P1, N2 = PL::N2, Q1 = PL::Q1;
   const int s_local = g / a.n_fpair, f = g - s_local * a.n_fpair;
   const int s = a.seg0 + s_local;
   const int ia = a.fa[f], ib = a.fb[f];
@@ -219,13 +219,14 @@ __device__ __forceinline__ void cta_tmem_end(uint32_t tbase, int warp) {
 // the N1-point DFT with Q1-point register DFTs.  Output slab layout: [pair-segment][c][b].
 // ------------------------------------------------------------------------------------------
 template <int LOGN, int BITS>
-__global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2)
+__global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
     k_phase1(BatchArgs a, const __grid_constant__ CUtensorMap slab_map) {
   using PL = Plan<LOGN>;
-  constexpr int P = PL::P, N1 = PL::N1, N2 = PL::N2, Q1 = PL::Q1, CW = PL::CW, PQ = PL::PQ;
+  constexpr int P = PL::P1, N1 = PL::N1, N2 = PL::N2, Q1 = PL::Q1, CW = PL::CW, PQ = PL::PQ;
   constexpr int LDP = PL::LDP1, LDQ = PL::LDQ1;
-  constexpr bool STAGED = PL::STAGED1;
-  constexpr int TILE = PL::TILE1, IPT = PL::IPT1, WPR = STAGED ? TILE * BITS / 32 : 1;  // words per tile row
+  using ST = typename PL::template Stage1<BITS>;
+  constexpr bool STAGED = ST::STAGED;
+  constexpr int TILE = ST::TILE, IPT = ST::IPT, WPR = STAGED ? ST::WPR : 1;  // words per IF per tile row
   // the warp's [N1][CW] output block leaves by one TMA store (a box is at most 256 rows)
   constexpr bool TMA_OUT = STAGED && N1 <= 256;
   static_assert(!TMA_OUT || (Q1 > 1 && N1 <= 256 && N1 * CW <= PL::REGION1 && (PL::REGION1 * 8) % 128 == 0),
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2)
   const int q1 = lane / CW, cw = lane % CW;
   float2* region = sm1 + warp * PL::REGION1;
   uint32_t* stage = reinterpret_cast<uint32_t*>(sm1 + PL::WARPS * PL::REGION1);  // [row][IF pair][WPR]
-  uint32_t* tslot = stage + PL::template stage_words<BITS>();
+  uint32_t* tslot = stage + ST::WORDS;
 
   uint32_t tbase = 0, t_tw = 0;
   if constexpr (Q1 > 1) {
@@ -356,9 +357,9 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2)
     // are staged in shared memory with cp.async, double-buffered so that the next tile's
     // words are in flight while the warps work on this one; every warp decodes its CW
     // columns from the stage.
-    constexpr int RS = PL::template stage_row<BITS>();   // words per staged row
-    constexpr int SB = N1 * RS;                          // words per stage buffer
-    constexpr int NB = PL::template stage_bufs<BITS>();  // 2: next tile in flight
+    constexpr int RS = ST::RS;   // words per staged row
+    constexpr int SB = N1 * RS;  // words per stage buffer
+    constexpr int NB = ST::NB;   // 2: next tile in flight
     const long long n_tiles = total_cols / TILE;
     const uint32_t stage_a = smem_addr(stage);
     // this thread's share of a tile's words: source offsets (words from the tile's first word
@@ -687,7 +688,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
 // return 1 for these kernels although two fit).  The kernels never wait on one another, so
 // a CTA beyond what fits simply starts later.
 template <typename K>
-static int ctas_per_sm(K kernel, int threads, size_t smem) {
+static int ctas_per_sm(K kernel, int threads, size_t smem, int tmem_cols) {
   cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   int n = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess) {
@@ -706,11 +707,12 @@ static int ctas_per_sm(K kernel, int threads, size_t smem) {
     const int by_threads = 2048 / threads;
     manual = by_regs < by_smem ? by_regs : by_smem;
     manual = manual < by_threads ? manual : by_threads;
-    if (manual > 2) manual = 2;  // tensor memory: at most two CTAs of 256 columns per SM
   } else {
     cudaGetLastError();
   }
   n = n > manual ? n : manual;
+  const int by_tmem = 512 / tmem_cols;  // each CTA holds tmem_cols of the SM's 512 columns
+  n = n < by_tmem ? n : by_tmem;
   return n < 1 ? 1 : n;
 }
 
@@ -744,23 +746,24 @@ static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st) {
   cudaGetDevice(&dev);
   if (attr_dev != dev) {
     cudaError_t e = cudaFuncSetAttribute(k_phase1<LOGN, BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)PL::template smem1<BITS>());
+                                         (int)PL::template Stage1<BITS>::SMEM);
     if (e != cudaSuccess) return e;
-    per_sm = ctas_per_sm(k_phase1<LOGN, BITS>, PL::THREADS, PL::template smem1<BITS>());
+    per_sm = ctas_per_sm(k_phase1<LOGN, BITS>, PL::THREADS, PL::template Stage1<BITS>::SMEM, PL::TCOLS1);
     attr_dev = dev;
   }
   alignas(64) CUtensorMap map;
   memset(&map, 0, sizeof map);
-  if constexpr (PL::STAGED1 && PL::N1 <= 256) {  // the kernel's TMA output path
+  using ST = typename PL::template Stage1<BITS>;
+  if constexpr (ST::STAGED && PL::N1 <= 256) {  // the kernel's TMA output path
     if ((reinterpret_cast<uintptr_t>(a.scratch) & 15) != 0) return cudaErrorMisalignedAddress;
     const cudaError_t e = encode_slab_map(&map, a.scratch, (long long)a.nseg * a.n_fpair * PL::N1, PL::N2, PL::CW, PL::N1);
     if (e != cudaSuccess) return e;
   }
   const long long cols = (long long)a.nseg * a.n_fpair * PL::N2;
-  const long long ctas = PL::STAGED1 ? cols / PL::TILE1  // one tile per CTA pass
+  const long long ctas = ST::STAGED ? cols / ST::TILE  // one tile per CTA pass
                                      : ((cols + PL::CW - 1) / PL::CW + PL::WARPS - 1) / PL::WARPS;
   const long long cap = (long long)per_sm * a.num_sms;
-  k_phase1<LOGN, BITS><<<(int)(ctas < cap ? ctas : cap), PL::THREADS, PL::template smem1<BITS>(), st>>>(a, map);
+  k_phase1<LOGN, BITS><<<(int)(ctas < cap ? ctas : cap), PL::THREADS, ST::SMEM, st>>>(a, map);
   return cudaGetLastError();
 }
 
@@ -788,7 +791,7 @@ cudaError_t run_phase2(const BatchArgs& a, cudaStream_t st) {
   if (attr_dev != dev) {
     cudaError_t e = cudaFuncSetAttribute(k_phase2<LOGN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL::SMEM2);
     if (e != cudaSuccess) return e;
-    per_sm = ctas_per_sm(k_phase2<LOGN>, PL::THREADS, PL::SMEM2);
+    per_sm = ctas_per_sm(k_phase2<LOGN>, PL::THREADS, PL::SMEM2, PL::TCOLS2);
     attr_dev = dev;
   }
   const long long warps = (long long)per_sm * a.num_sms * PL::WARPS;

@@ -79,6 +79,22 @@ def test_bits(pol, orc, bits):
     assert_close(got, ref, [(0, 1)], TOL)
 
 
+@pytest.mark.parametrize("logn", [13, 14, 15, 16, 17, 18, 19])
+@pytest.mark.parametrize("bits", [1, 2, 4, 8])
+def test_staged_sizes_every_width(pol, orc, logn, bits):
+    """Every (size, sample width) of the shared-memory-staged phase 1: tile widths, stage
+    buffers and the TMA/scattered output paths differ per pair.  Three IFs, so one FFT pair
+    has no IF b; the window alternates between rect and Hann."""
+    n_fft, nseg = 1 << logn, 3
+    n = n_fft * nseg
+    packed = _random_streams(1000 + 10 * logn + bits, 3, n, bits)
+    hann = (logn + bits) % 2 == 1
+    got = _run(pol, packed, bits, n_fft, n, window="hann" if hann else "rect", pairs=[(0, 1)])
+    ref = _oracle(orc, packed, bits, n_fft, n, window_kind=1 if hann else 0, pairs=[(0, 1)])
+    assert got["n_segments"] == nseg
+    assert_close(got, ref, [(0, 1)], TOL)
+
+
 def test_paper_config_one_integration(pol, orc):
     """4 IFs, 2-bit, N = 131072, 61 segments (one 1-s integration), three-line spectrum."""
     packed, meta = synth.config_paper(n_segments=61)
