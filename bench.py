@@ -304,16 +304,19 @@ def run_ours(args, rank, world, local_rank, dist):
         n_host = min(len(unique), 4)
         pinned = [torch.from_numpy(unique[i]).pin_memory() for i in range(n_host)]
         host = [p.numpy().view(np.uint32) for p in pinned]
+        nb = N_FFT // 2 + 1
+        outs = {k: torch.empty(shape, dtype=torch.float32, pin_memory=True).numpy()
+                for k, shape in (("autos", (N_IF, nb)), ("cross", (N_PAIR, nb, 2)), ("stokes", (N_PAIR, 4, nb)))}
         for i in range(2):
             sp.feed([host[i % n_host][j] for j in range(N_IF)], SAMPLES_PER_IF, on_device=False)
-            sp.integrate()
+            sp.integrate(out=outs)
         e2e_steps = max(3, min(args.steps, args.e2e_steps))
         torch.cuda.synchronize(dev)
         barrier()
         t0 = time.perf_counter()
         for i in range(e2e_steps):
             sp.feed([host[i % n_host][j] for j in range(N_IF)], SAMPLES_PER_IF, on_device=False)
-            out = sp.integrate()
+            out = sp.integrate(out=outs)
             assert out["n_segments"] == SEGS
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0

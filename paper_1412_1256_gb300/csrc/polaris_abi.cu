@@ -735,13 +735,18 @@ extern "C" int spectrometer_integrate(polaris_spec* s, const polaris_stokes_para
   rc = spectrometer_integrate_device(s, prm, s->d_out_autos, s->n_pair ? s->d_out_cross : nullptr,
                                      s->n_pair ? s->d_out_stokes : nullptr, n_segments_out, nullptr);
   if (rc) return rc;
+  // stream-ordered after the readout; one synchronisation for all three (direct copies when
+  // the caller's buffers are pinned)
   if (autos)
-    CUDA_OR_FAIL(s, cudaMemcpy(autos, s->d_out_autos, (size_t)s->nbin * 4 * s->n_if, cudaMemcpyDeviceToHost));
+    CUDA_OR_FAIL(s, cudaMemcpyAsync(autos, s->d_out_autos, (size_t)s->nbin * 4 * s->n_if, cudaMemcpyDeviceToHost,
+                                    nullptr));
   if (cross && s->n_pair)
-    CUDA_OR_FAIL(s, cudaMemcpy(cross, s->d_out_cross, (size_t)s->nbin * 8 * s->n_pair, cudaMemcpyDeviceToHost));
+    CUDA_OR_FAIL(s, cudaMemcpyAsync(cross, s->d_out_cross, (size_t)s->nbin * 8 * s->n_pair, cudaMemcpyDeviceToHost,
+                                    nullptr));
   if (stokes && s->n_pair)
-    CUDA_OR_FAIL(s, cudaMemcpy(stokes, s->d_out_stokes, (size_t)s->nbin * 16 * s->n_pair, cudaMemcpyDeviceToHost));
-  CUDA_OR_FAIL(s, cudaDeviceSynchronize());
+    CUDA_OR_FAIL(s, cudaMemcpyAsync(stokes, s->d_out_stokes, (size_t)s->nbin * 16 * s->n_pair,
+                                    cudaMemcpyDeviceToHost, nullptr));
+  CUDA_OR_FAIL(s, cudaStreamSynchronize(nullptr));
   return POLARIS_OK;
 }
 

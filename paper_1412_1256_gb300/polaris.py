@@ -196,19 +196,36 @@ class Spectrometer:
             p.gains = g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         return p, g
 
-    def integrate(self, feed: int = FEED_LINEAR, psi: float = 0.0, gains=None):
-        """Close the integration; returns dict(autos, cross (complex), stokes, n_segments) as numpy."""
+    def integrate(self, feed: int = FEED_LINEAR, psi: float = 0.0, gains=None, out=None):
+        """Close the integration; returns dict(autos, cross (complex64), stokes, n_segments) as numpy.
+
+        out: optional dict of preallocated C-contiguous float32 arrays 'autos' [n_if, nb],
+        'cross' [n_pair, nb, 2], 'stokes' [n_pair, 4, nb] to fill (views of pinned host
+        memory make the device-to-host copies direct); missing entries are allocated."""
         nb, npair = self.n_bins, self.n_pairs
-        autos = np.empty((self.n_if, nb), np.float32)
-        cross = np.empty((max(npair, 1), nb, 2), np.float32)
-        stokes = np.empty((max(npair, 1), 4, nb), np.float32)
+        out = {} if out is None else out
+
+        def buf(key, shape):
+            a = out.get(key)
+            if a is None:
+                return np.empty(shape, np.float32)
+            if a.dtype != np.float32 or tuple(a.shape) != shape or not a.flags["C_CONTIGUOUS"]:
+                raise ValueError(f"out[{key!r}] must be a C-contiguous float32 array of shape {shape}")
+            return a
+
+        autos = buf("autos", (self.n_if, nb))
+        cross = buf("cross", (npair, nb, 2)) if npair else None
+        stokes = buf("stokes", (npair, 4, nb)) if npair else None
         nseg = ctypes.c_int64(0)
         p, g = self._params(feed, psi, gains)
-        self._check(load().spectrometer_integrate(self._h, ctypes.byref(p), autos.ctypes.data, cross.ctypes.data,
-                                                  stokes.ctypes.data, ctypes.byref(nseg)))
+        self._check(load().spectrometer_integrate(self._h, ctypes.byref(p), autos.ctypes.data,
+                                                  None if cross is None else cross.ctypes.data,
+                                                  None if stokes is None else stokes.ctypes.data, ctypes.byref(nseg)))
         del g
-        cross = cross[:npair]
-        return {"autos": autos, "cross": cross[..., 0] + 1j * cross[..., 1], "stokes": stokes[:npair],
+        if cross is None:
+            cross = np.empty((0, nb, 2), np.float32)
+            stokes = np.empty((0, 4, nb), np.float32)
+        return {"autos": autos, "cross": cross.view(np.complex64)[..., 0], "stokes": stokes,
                 "n_segments": int(nseg.value)}
 
     def integrate_device(self, autos, cross, stokes, feed: int = FEED_LINEAR, psi: float = 0.0, gains=None,
