@@ -84,10 +84,18 @@ def fp32_peak_tflops(num_sms: int, sm_mhz: float) -> float:
     return num_sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def source_digest() -> str:
+KERNEL_SOURCES = {
+    # files whose contents define each timed kernel (a traffic record is valid for these only)
+    "phase1_decode_rowdft": ("polaris_device.cuh", "polaris_kernels.cuh", "polaris_n17.cu"),
+    "phase2_coldft_correlate": ("polaris_device.cuh", "polaris_kernels.cuh", "polaris_n17.cu"),
+    "readout_stokes": ("polaris_abi.cu",),
+}
+
+
+def source_digest(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1412_1256_gb300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(ROOT, "paper_1412_1256_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -102,7 +110,7 @@ def recorded_traffic(kernel: str):
         parts = line.split()
         if len(parts) == 2 and not line.startswith("#"):
             vals[parts[0]] = parts[1]
-    if vals.get("source_digest") != source_digest():
+    if vals.get("source_digest") != source_digest(kernel):
         return None
     try:
         return float(vals["dram_bytes_per_segment_pair"])
