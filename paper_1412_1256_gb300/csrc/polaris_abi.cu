@@ -18,8 +18,8 @@
 namespace polaris {
 // per-size phase runners, one translation unit each (polaris_n<LOGN>.cu)
 #define POLARIS_DECLARE(LOGN)                                                    \
-  extern template cudaError_t run_phase1<LOGN>(const BatchArgs&, cudaStream_t); \
-  extern template cudaError_t run_phase2<LOGN>(const BatchArgs&, cudaStream_t);
+  extern template cudaError_t run_phase1<LOGN>(const BatchArgs&, cudaStream_t, bool); \
+  extern template cudaError_t run_phase2<LOGN>(const BatchArgs&, cudaStream_t, bool);
 POLARIS_DECLARE(4)
 POLARIS_DECLARE(5)
 POLARIS_DECLARE(6)
@@ -38,7 +38,8 @@ POLARIS_DECLARE(18)
 POLARIS_DECLARE(19)
 #undef POLARIS_DECLARE
 
-typedef cudaError_t (*phase_fn)(const BatchArgs&, cudaStream_t);
+// (args, stream, programmatic dependent launch on the predecessor in `stream`)
+typedef cudaError_t (*phase_fn)(const BatchArgs&, cudaStream_t, bool);
 #define POLARIS_ROW(LOGN) {run_phase1<LOGN>, run_phase2<LOGN>}
 static const phase_fn kPhases[20][2] = {
     {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr},
@@ -94,6 +95,7 @@ __global__ void __launch_bounds__(kReadoutThreads) k_readout(ReadoutArgs a) {
   constexpr int TD = N1 >= kReadoutMinTile ? 1 : kReadoutMinTile / N1, TE = TD * N1;
   constexpr int PT = (TE + kReadoutThreads - 1) / kReadoutThreads;  // entries per thread
   __shared__ float4 tile[TD * (N1 + 1)];
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");  // accumulators complete (dependent launch)
   const int f = blockIdx.y, N2 = a.N2;
   const int d0 = blockIdx.x * TD;
   const size_t fo = (size_t)f * a.native;
@@ -181,19 +183,25 @@ static dim3 readout_grid(int N1, int N2, int n_fpair) {
   return dim3((unsigned)((N2 / 2 + 1 + td - 1) / td), (unsigned)n_fpair);
 }
 
-static cudaError_t launch_readout(const ReadoutArgs& r, int n_fpair, cudaStream_t st) {
-  const dim3 grid = readout_grid(r.N1, r.N2, n_fpair);
+static cudaError_t launch_readout(const ReadoutArgs& r, int n_fpair, cudaStream_t st, bool pdl) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = readout_grid(r.N1, r.N2, n_fpair);
+  cfg.blockDim = dim3(kReadoutThreads);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
   switch (r.N1) {
-#define POLARIS_RO(LN1)                                        \
-  case 1 << LN1:                                               \
-    k_readout<LN1><<<grid, kReadoutThreads, 0, st>>>(r);        \
-    break;
+#define POLARIS_RO(LN1)                                       \
+  case 1 << LN1:                                              \
+    return cudaLaunchKernelEx(&cfg, k_readout<LN1>, r);
     POLARIS_RO(1) POLARIS_RO(2) POLARIS_RO(3) POLARIS_RO(4) POLARIS_RO(5) POLARIS_RO(6) POLARIS_RO(7)
     POLARIS_RO(8) POLARIS_RO(9) POLARIS_RO(10)
 #undef POLARIS_RO
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 static int host_plan_n2(int logn) { return 1 << plan_log_n2(logn); }
@@ -618,7 +626,21 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
   a.fp64 = s->accum_fp64;
   a.bits = s->bits;
   a.num_sms = s->num_sms;
-  if (nseg > 0) {
+  const phase_fn f1 = kPhases[s->logn][0], f2 = kPhases[s->logn][1];
+  if (nseg > 0 && nseg <= s->max_batch) {
+    // one pass: both phases on the caller's stream; phase 2 is a programmatic dependent
+    // launch (its CTAs set up while phase 1 drains) unless launches are being timed
+    a.seg0 = 0;
+    a.nseg = (int)nseg;
+    a.scratch = s->d_scratch;
+    const bool pdl = st != nullptr && !s->profiling;
+    cudaError_t e = counted_launch(s, 0, st, [&]() { return f1(a, st, false); });
+    if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "phase-1 launch: %s", cudaGetErrorString(e));
+    e = counted_launch(s, 1, st, [&]() { return f2(a, st, pdl); });
+    if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "phase-2 launch: %s", cudaGetErrorString(e));
+  } else if (nseg > 0) {
+    // several passes: phase 1 and phase 2 on two internal streams, pass b + 1's phase 1
+    // overlapping pass b's phase 2 (alternate slab halves).
     // fork: both internal streams start after everything queued so far on the caller's stream
     CUDA_OR_FAIL(s, cudaEventRecord(s->ev_fork, st));
     CUDA_OR_FAIL(s, cudaStreamWaitEvent(s->st_p1, s->ev_fork, 0));
@@ -630,12 +652,11 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
       a.scratch = s->d_scratch + (size_t)(b & 1) * s->slab_half;
       // phase 1 of batch b may overwrite its slab half once phase 2 of batch b-2 has read it
       if (b >= 2) CUDA_OR_FAIL(s, cudaStreamWaitEvent(s->st_p1, s->ev_p2[b & 1], 0));
-      const phase_fn f1 = kPhases[s->logn][0], f2 = kPhases[s->logn][1];
-      cudaError_t e = counted_launch(s, 0, s->st_p1, [&]() { return f1(a, s->st_p1); });
+      cudaError_t e = counted_launch(s, 0, s->st_p1, [&]() { return f1(a, s->st_p1, false); });
       if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "phase-1 launch: %s", cudaGetErrorString(e));
       CUDA_OR_FAIL(s, cudaEventRecord(s->ev_p1[b & 1], s->st_p1));
       CUDA_OR_FAIL(s, cudaStreamWaitEvent(s->st_p2, s->ev_p1[b & 1], 0));
-      e = counted_launch(s, 1, s->st_p2, [&]() { return f2(a, s->st_p2); });
+      e = counted_launch(s, 1, s->st_p2, [&]() { return f2(a, s->st_p2, false); });
       if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "phase-2 launch: %s", cudaGetErrorString(e));
       CUDA_OR_FAIL(s, cudaEventRecord(s->ev_p2[b & 1], s->st_p2));
     }
@@ -719,7 +740,8 @@ extern "C" int spectrometer_integrate_device(polaris_spec* s, const polaris_stok
   r.autos = d_autos;
   r.cross = d_cross;
   r.stokes = d_stokes;
-  CUDA_OR_FAIL(s, counted_launch(s, 2, st, [&]() { return launch_readout(r, s->n_fpair, st); }));
+  const bool pdl = st != nullptr && !s->profiling;  // dependent launch on the last phase 2
+  CUDA_OR_FAIL(s, counted_launch(s, 2, st, [&]() { return launch_readout(r, s->n_fpair, st, pdl); }));
   // (the readout has cleared the accumulators it read)
   if (n_segments_out) *n_segments_out = s->seg_acc;
   s->seg_acc = 0;
@@ -995,7 +1017,7 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
   for (int64_t s0 = 0; s0 < nseg; s0 += batch) {
     a.seg0 = (int)s0;
     a.nseg = (int)(nseg - s0 < batch ? nseg - s0 : batch);
-    for (int ph = 0; ph < 2 && e == cudaSuccess; ++ph) e = kPhases[logn][ph](a, st);
+    for (int ph = 0; ph < 2 && e == cudaSuccess; ++ph) e = kPhases[logn][ph](a, st, ph == 1 && st != nullptr);
     if (e != cudaSuccess) return set_err(nullptr, POLARIS_ECUDA, "no-alloc FFT-correlator: %s", cudaGetErrorString(e));
   }
   // readout (same kernel as spectrometer_integrate_device)
@@ -1038,7 +1060,7 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
   r.autos = d_autos;
   r.cross = n_pair ? d_cross : nullptr;
   r.stokes = n_pair ? d_stokes : nullptr;
-  e = launch_readout(r, nf, st);
+  e = launch_readout(r, nf, st, st != nullptr);
   if (e != cudaSuccess) return set_err(nullptr, POLARIS_ECUDA, "no-alloc readout: %s", cudaGetErrorString(e));
   if (n_segments_out) *n_segments_out = nseg;
   return POLARIS_OK;

@@ -100,6 +100,13 @@ __device__ __forceinline__ void tma_store_2d_elect(const CUtensorMap* map, const
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// programmatic dependent launch: a kernel launched with programmatic stream serialisation may
+// start before its predecessor in the stream ends; pdl_wait() returns once the predecessor
+// has completed and its memory operations are visible (at once for an ordinary launch).
+// pdl_trigger() lets the successor's CTAs be scheduled as soon as every CTA of this grid has
+// triggered or exited.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
 // ------------------------------------------------------------------------------------------
 // tensor memory (TMEM) as per-thread storage: warp w reaches lanes 32 (w % 4) .. +31; a
@@ -399,6 +406,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
       if constexpr (NB == 2) {
         if (next < n_tiles) issue(next, buf ^ 1);
       }
+      if (next >= n_tiles) pdl_trigger();  // this CTA's last tile: phase 2 may be scheduled
       const int g = (int)(tile / (N2 / TILE)), b0 = (int)(tile % (N2 / TILE)) * TILE;
       const int f = g % a.n_fpair;
       const bool has_b = a.fb[f] >= 0;
@@ -481,6 +489,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
 
   for (int k = tid; k < N2; k += PL::THREADS) tw2[k + (k >> 5)] = tw_small<N2>(k);
   const uint32_t tbase = cta_tmem_begin<PL::TCOLS2>(tslot, warp);  // (its barrier also publishes tw2)
+  pdl_wait();  // the slab written by phase 1 (and the accumulators cleared by the readout) are visible
   const uint32_t t_acc = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * (PL::TCOLS2 / 2));
   const uint32_t t_tw = t_acc + TACC;
 
@@ -677,6 +686,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
       }
     }
   }
+  pdl_trigger();
   cta_tmem_end<PL::TCOLS2>(tbase, warp);
 }
 
@@ -769,7 +779,7 @@ static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st) {
 
 // phase 1 of one batch
 template <int LOGN>
-cudaError_t run_phase1(const BatchArgs& a, cudaStream_t st) {
+cudaError_t run_phase1(const BatchArgs& a, cudaStream_t st, bool /*pdl: phase 1 is always an ordinary launch*/) {
   if (a.nseg <= 0) return cudaSuccess;
   switch (a.bits) {
     case 1: return launch_phase1<LOGN, 1>(a, st);
@@ -782,7 +792,7 @@ cudaError_t run_phase1(const BatchArgs& a, cudaStream_t st) {
 
 // phase 2 of one batch: items (pair, unit group, range of segments), about one per warp
 template <int LOGN>
-cudaError_t run_phase2(const BatchArgs& a, cudaStream_t st) {
+cudaError_t run_phase2(const BatchArgs& a, cudaStream_t st, bool pdl) {
   using PL = Plan<LOGN>;
   if (a.nseg <= 0) return cudaSuccess;
   static int attr_dev = -1, per_sm = 1;
@@ -802,12 +812,21 @@ cudaError_t run_phase2(const BatchArgs& a, cudaStream_t st) {
   const long long n_items = groups * ((R + range_len - 1) / range_len);
   const long long ctas = (n_items + PL::WARPS - 1) / PL::WARPS;
   const long long cap = (long long)per_sm * a.num_sms;
-  k_phase2<LOGN><<<(int)(ctas < cap ? ctas : cap), PL::THREADS, PL::SMEM2, st>>>(a, (int)range_len);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(ctas < cap ? ctas : cap));
+  cfg.blockDim = dim3(PL::THREADS);
+  cfg.dynamicSmemBytes = PL::SMEM2;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k_phase2<LOGN>, a, (int)range_len);
 }
 
 }  // namespace polaris
 
 #define POLARIS_INSTANTIATE(LOGN)                                                          \
-  template cudaError_t polaris::run_phase1<LOGN>(const polaris::BatchArgs&, cudaStream_t); \
-  template cudaError_t polaris::run_phase2<LOGN>(const polaris::BatchArgs&, cudaStream_t);
+  template cudaError_t polaris::run_phase1<LOGN>(const polaris::BatchArgs&, cudaStream_t, bool); \
+  template cudaError_t polaris::run_phase2<LOGN>(const polaris::BatchArgs&, cudaStream_t, bool);
