@@ -96,6 +96,8 @@ __global__ void __launch_bounds__(kReadoutThreads) k_readout(ReadoutArgs a) {
   constexpr int PT = (TE + kReadoutThreads - 1) / kReadoutThreads;  // entries per thread
   __shared__ float4 tile[TD * (N1 + 1)];
   asm volatile("griddepcontrol.wait;\n" ::: "memory");  // accumulators complete (dependent launch)
+  // the next feed's phase 1 may set up alongside (it waits for this grid before touching data)
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   const int f = blockIdx.y, N2 = a.N2;
   const int d0 = blockIdx.x * TD;
   const size_t fo = (size_t)f * a.native;
@@ -628,13 +630,14 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
   a.num_sms = s->num_sms;
   const phase_fn f1 = kPhases[s->logn][0], f2 = kPhases[s->logn][1];
   if (nseg > 0 && nseg <= s->max_batch) {
-    // one pass: both phases on the caller's stream; phase 2 is a programmatic dependent
-    // launch (its CTAs set up while phase 1 drains) unless launches are being timed
+    // one pass: both phases on the caller's stream, each a programmatic dependent launch
+    // (its CTAs set up while the previous kernel drains, then wait for it) unless launches
+    // are being timed
     a.seg0 = 0;
     a.nseg = (int)nseg;
     a.scratch = s->d_scratch;
     const bool pdl = st != nullptr && !s->profiling;
-    cudaError_t e = counted_launch(s, 0, st, [&]() { return f1(a, st, false); });
+    cudaError_t e = counted_launch(s, 0, st, [&]() { return f1(a, st, pdl); });
     if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "phase-1 launch: %s", cudaGetErrorString(e));
     e = counted_launch(s, 1, st, [&]() { return f2(a, st, pdl); });
     if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "phase-2 launch: %s", cudaGetErrorString(e));
@@ -1017,7 +1020,7 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
   for (int64_t s0 = 0; s0 < nseg; s0 += batch) {
     a.seg0 = (int)s0;
     a.nseg = (int)(nseg - s0 < batch ? nseg - s0 : batch);
-    for (int ph = 0; ph < 2 && e == cudaSuccess; ++ph) e = kPhases[logn][ph](a, st, ph == 1 && st != nullptr);
+    for (int ph = 0; ph < 2 && e == cudaSuccess; ++ph) e = kPhases[logn][ph](a, st, st != nullptr);
     if (e != cudaSuccess) return set_err(nullptr, POLARIS_ECUDA, "no-alloc FFT-correlator: %s", cudaGetErrorString(e));
   }
   // readout (same kernel as spectrometer_integrate_device)

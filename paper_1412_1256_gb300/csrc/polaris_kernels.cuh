@@ -263,6 +263,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
     });
     tmem_wait_st();
   }
+  pdl_wait();  // the input and the slab may be touched from here on (dependent launch)
 
   // the second half of the work on one column group: twiddle, transpose, Q1-point DFTs, store.
   // After the transpose lane (q1, cw) holds, for p = r Q1 + q1, the Q1 values of row p; its
@@ -749,7 +750,7 @@ static cudaError_t encode_slab_map(CUtensorMap* map, float2* slab, long long row
 }
 
 template <int LOGN, int BITS>
-static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st) {
+static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st, bool pdl) {
   using PL = Plan<LOGN>;
   static int attr_dev = -1, per_sm = 1;
   int dev = 0;
@@ -773,19 +774,28 @@ static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st) {
   const long long ctas = ST::STAGED ? cols / ST::TILE  // one tile per CTA pass
                                      : ((cols + PL::CW - 1) / PL::CW + PL::WARPS - 1) / PL::WARPS;
   const long long cap = (long long)per_sm * a.num_sms;
-  k_phase1<LOGN, BITS><<<(int)(ctas < cap ? ctas : cap), PL::THREADS, ST::SMEM, st>>>(a, map);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(ctas < cap ? ctas : cap));
+  cfg.blockDim = dim3(PL::THREADS);
+  cfg.dynamicSmemBytes = ST::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, k_phase1<LOGN, BITS>, a, map);
 }
 
 // phase 1 of one batch
 template <int LOGN>
-cudaError_t run_phase1(const BatchArgs& a, cudaStream_t st, bool /*pdl: phase 1 is always an ordinary launch*/) {
+cudaError_t run_phase1(const BatchArgs& a, cudaStream_t st, bool pdl) {
   if (a.nseg <= 0) return cudaSuccess;
   switch (a.bits) {
-    case 1: return launch_phase1<LOGN, 1>(a, st);
-    case 2: return launch_phase1<LOGN, 2>(a, st);
-    case 4: return launch_phase1<LOGN, 4>(a, st);
-    case 8: return launch_phase1<LOGN, 8>(a, st);
+    case 1: return launch_phase1<LOGN, 1>(a, st, pdl);
+    case 2: return launch_phase1<LOGN, 2>(a, st, pdl);
+    case 4: return launch_phase1<LOGN, 4>(a, st, pdl);
+    case 8: return launch_phase1<LOGN, 8>(a, st, pdl);
     default: return cudaErrorInvalidValue;
   }
 }
