@@ -334,6 +334,51 @@ def run_ours(args, rank, world, local_rank, dist):
             dt = float(tt.item())
         e2e_value = world * e2e_steps * SAMPLES_PER_STEP / dt / 1e6
 
+    # variants of the same workload (NEXT-4): 50% overlap (hop = N/2, Sec. 3.1) and the
+    # code-histogram statistics (Sec. 2 bit distribution), each through the same API
+    variants = None
+    if not args.no_variants:
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        def timed(spv, nsteps):
+            def stepv(i):
+                sec = ring[i % ring_n]
+                spv.feed([sec[j] for j in range(N_IF)], SAMPLES_PER_IF, on_device=True, stream=stream)
+                return spv.integrate_device(autos, cross, stokes, stream=stream)
+
+            for i in range(3):
+                stepv(i)
+            torch.cuda.synchronize(dev)
+            segs = 0
+            ev0.record(stream)
+            for i in range(nsteps):
+                segs = stepv(3 + i)
+            ev1.record(stream)
+            torch.cuda.synchronize(dev)
+            return ev0.elapsed_time(ev1) / nsteps, segs
+
+        nv = max(10, min(args.steps, 100))
+        variants = {}
+        with polaris.Spectrometer(N_IF, BITS, N_FFT, hop=N_FFT // 2, device=local_rank) as spo:
+            ms, segs = timed(spo, nv)
+        variants["overlap_50"] = {"hop": N_FFT // 2, "segments_per_step": segs, "ms_per_step": ms,
+                                  "value": world * SAMPLES_PER_STEP / (ms * 1e-3) / 1e6, "unit": "Msample/s",
+                                  "steps": nv}
+        with polaris.Spectrometer(N_IF, BITS, N_FFT, device=local_rank, code_stats=True) as sps:
+            ms, segs = timed(sps, nv)
+            sps.set_profiling(True)
+            for i in range(10):
+                sps.feed([ring[i % ring_n][j] for j in range(N_IF)], SAMPLES_PER_IF, on_device=True, stream=stream)
+                sps.integrate_device(autos, cross, stokes, stream=stream)
+            torch.cuda.synchronize(dev)
+            kh = sps.kernel_times()["code_histogram"]
+            sps.set_profiling(False)
+            h = sps.code_histogram()
+            assert int(h.sum()) == N_IF * N_FFT * SEGS * (3 + nv + 10)
+        variants["code_stats"] = {"ms_per_step": ms, "value": world * SAMPLES_PER_STEP / (ms * 1e-3) / 1e6,
+                                  "unit": "Msample/s", "steps": nv,
+                                  "histogram_kernel_ms": kh[0] / kh[1] if kh[1] else None}
+
     sp.close()
     if rank != 0:
         return
@@ -345,7 +390,7 @@ def run_ours(args, rank, world, local_rank, dist):
     kernels = {}
     total_kt = sum(v[0] for v in kt.values()) or 1.0
     for k, (ms, n) in kt.items():
-        if n:
+        if n and k in flops:
             per_step = flops[k]  # flops per step for this kernel
             launches_per_step = n / prof_steps
             kernels[k] = {"avg_ms": ms / n, "launches": n, "share": ms / total_kt,
@@ -389,6 +434,8 @@ def run_ours(args, rank, world, local_rank, dist):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if variants is not None:
+        line["variants"] = variants
     if world == 1 and not args.no_cpu_baseline:
         v, dt = time_oracle(unique, args.cpu_segs, args.cpu_repeats)
         line["cpu_baseline"] = {"value": v, "unit": "Msample/s", "cores": 1, "kind": "oracle",
@@ -412,6 +459,7 @@ def main():
                     help="segments per kernel pass (0: the library's default, sized to keep the slab in L2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-variants", action="store_true", help="skip the overlap / code-statistics variants")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -77,7 +77,11 @@ typedef struct polaris_spec polaris_spec; /* opaque, library-owned */
  *   device      CUDA device ordinal.
  *   max_batch_segments  segments processed per kernel pass (bounds the device
  *               scratch: 2 * max_batch_segments * n_fft * 8 bytes per pair);
- *               0 selects the default (passes of at least 64 segments). */
+ *               0 selects the default (passes of at least 64 segments).
+ *   code_stats  1: also count, per IF, how often each b-bit code occurs in the
+ *               segments that feed() integrates (the bit distribution used for
+ *               total-power measurement, Sec. 2 and Sec. 3.2.2); read with
+ *               spectrometer_code_histogram.  0: no counting (no extra work). */
 typedef struct {
   int n_if;
   int bits;
@@ -90,6 +94,7 @@ typedef struct {
   int accum_fp64;
   int device;
   int max_batch_segments;
+  int code_stats;
 } polaris_config;
 
 /* Stokes parameters for integrate (Eq. 2): feed type, parallactic angle psi_m
@@ -158,7 +163,8 @@ const char* spectrometer_last_error(const polaris_spec* s);
  * waits for those events and returns, per kind, the summed device time in ms and the
  * launch count since profiling began or since the previous query (kinds: 0 = phase 1,
  * decode/window/row DFT; 1 = phase 2, column DFT/correlate/accumulate; 2 = readout and
- * Stokes).  n is the length of both arrays and must be >= 3. */
+ * Stokes; 3 = code histogram).  n is the length of both arrays and must be >= 3; kinds
+ * >= n are not reported. */
 int64_t spectrometer_kernel_launches(const polaris_spec* s);
 int spectrometer_set_profiling(polaris_spec* s, int on);
 int spectrometer_kernel_times(polaris_spec* s, double* ms, int64_t* launches, int n);
@@ -187,10 +193,34 @@ int spectrometer_kernel_times(polaris_spec* s, double* ms, int64_t* launches, in
  * previous call's contents (each call zeroes the accumulators it needs): calls whose
  * GPU work overlaps -- on different streams or devices' shared host threads -- race on
  * it and must be ordered by the caller.  A configuration whose accumulators, tables and
- * one segment of slab exceed 32 MiB is rejected with POLARIS_EINVAL and a message. */
+ * one segment of slab exceed 32 MiB is rejected with POLARIS_EINVAL and a message.
+ * cfg->code_stats is ignored (no histogram is kept). */
 int spectrometer_run_noalloc(const polaris_config* cfg, const void* const* d_packed, int64_t n_samples_per_if,
                              const polaris_stokes_params* params, float* d_autos, float* d_cross, float* d_stokes,
                              int64_t* n_segments_out, void* cuda_stream);
+
+/* Code histogram: the bit distribution of the digitised signal, from which PolariS
+ * derives each IF's total power (Sec. 2; linearity of that measurement, Sec. 3.2.2).  counts: host array of n_if * 2^bits uint64, filled
+ * with counts[i * 2^bits + c] = number of samples of IF i with code c, summed over
+ * every segment integrated since the spectrometer was created or last reset (a
+ * sample in two overlapping segments counts twice).  reset != 0 zeroes the counts
+ * after reading them.  Synchronises with the work queued so far.  Returns
+ * POLARIS_ESTATE if the spectrometer was created with code_stats = 0. */
+int spectrometer_code_histogram(polaris_spec* s, uint64_t* counts, int reset);
+
+/* Total power of one IF from its code histogram (counts: 2^bits entries; host-only
+ * arithmetic in FP64).  Our reading of the bit-distribution method (the cited
+ * scheme is not reproduced in the paper):
+ *   moment2  = sum_c level(c)^2 counts[c] / sum_c counts[c], with the decoded levels
+ *              (2c - (2^b - 1) for b < 8, int8 for b = 8): the power of the digitised
+ *              signal in level units (a measure of input power for 4 and 8 bits);
+ *   sigma_over_threshold (2-bit only) = 1 / (sqrt(2) erfcinv(p_outer)), p_outer the
+ *              fraction of the two outer codes: the rms of a zero-mean Gaussian input
+ *              in units of the sampler threshold; NaN for other widths or when
+ *              p_outer is 0 or 1.
+ * Either output pointer may be NULL.  Returns POLARIS_EINVAL for a bad width, NULL
+ * counts or an empty histogram. */
+int polaris_power_from_histogram(int bits, const uint64_t* counts, double* moment2, double* sigma_over_threshold);
 
 /* Test hook: cap the bytes of device memory that later spectrometer_create
  * calls may allocate (-1 = no cap), so that allocation failure can be tested

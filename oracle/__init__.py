@@ -16,4 +16,6 @@ from .oracle import (  # noqa: F401
     spectra_levels,
     spectrometer,
     default_pairs,
+    code_histogram,
+    power,
 )

@@ -57,12 +57,16 @@ def _load():
                 ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _F, ctypes.c_int, _I32,
                 ctypes.POINTER(_D), ctypes.c_int64, _D, _D, _I64,
             ]
+            lib.oracle_code_histogram.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                                  ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
+                                                  ctypes.POINTER(ctypes.c_uint64)]
+            lib.oracle_power.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), _D, _D]
             lib.oracle_accumulate.argtypes = [
                 ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _F, ctypes.c_int, _I32,
                 ctypes.POINTER(_U32), ctypes.c_int64, _D, _D, _I64,
             ]
             for f in ("oracle_decode", "oracle_window", "oracle_dft", "oracle_fft", "oracle_stokes", "oracle_accumulate",
-                      "oracle_spectra_levels"):
+                      "oracle_spectra_levels", "oracle_code_histogram", "oracle_power"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -194,3 +198,24 @@ def spectrometer(packed, bits: int, n_fft: int, n_samples: int, hop: int | None 
         ga, gb = (1.0, 1.0) if gains is None else gains[p]
         st[p] = stokes(autos[a], autos[b], cross[p], feed=feed, psi=psi, ga=ga, gb=gb)
     return {"autos": autos, "cross": cross, "stokes": st, "n_segments": nseg}
+
+
+def code_histogram(packed, bits: int, n_fft: int, n_samples: int, hop: int | None = None) -> np.ndarray:
+    """Per-IF code counts [n_if, 2^bits] over every whole segment (Sec. 2 bit distribution)."""
+    hop = n_fft if hop is None else hop
+    words = [np.ascontiguousarray(p, dtype=np.uint32) for p in packed]
+    arr = (ctypes.c_void_p * len(words))(*[w.ctypes.data for w in words])
+    out = np.zeros((len(words), 1 << bits), np.uint64)
+    _check(_load().oracle_code_histogram(len(words), bits, n_fft, hop, arr, n_samples,
+                                         out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))), "code_histogram")
+    return out
+
+
+def power(bits: int, counts) -> tuple[float, float]:
+    """(moment2, sigma_over_threshold) of one IF's code histogram."""
+    c = np.ascontiguousarray(np.asarray(counts, dtype=np.uint64).reshape(-1))
+    m2 = np.zeros(1)
+    sg = np.zeros(1)
+    _check(_load().oracle_power(bits, c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _p(m2, _D), _p(sg, _D)),
+           "power")
+    return float(m2[0]), float(sg[0])

@@ -254,3 +254,67 @@ int oracle_accumulate(int n_if, int bits, int64_t n_fft, int64_t hop, int window
   free(lev);
   return rc;
 }
+
+/* Bit distribution (Sec. 2: each IF's total power comes from the histogram of its
+ * digitised samples; Sec. 3.2.2 tests that measurement's linearity).  counts[i * 2^bits
+ * + c] = number of samples with code c among the samples of every whole segment of IF i
+ * (segment s = samples [s*hop, s*hop + n_fft)), so a sample in two overlapping segments
+ * counts twice.  Plain loop over segments and samples. */
+int oracle_code_histogram(int n_if, int bits, int64_t n_fft, int64_t hop, const uint32_t* const* packed,
+                          int64_t n_samples, uint64_t* counts) {
+  if (n_if < 1 || !(bits == 1 || bits == 2 || bits == 4 || bits == 8) || n_fft < 1 || hop < 1 || !packed ||
+      !counts || n_samples < 0)
+    return OR_EINVAL;
+  const int nc = 1 << bits;
+  const int64_t per_word = 32 / bits;
+  const uint32_t mask = (uint32_t)nc - 1u;
+  memset(counts, 0, sizeof(uint64_t) * (size_t)n_if * (size_t)nc);
+  const int64_t n_seg = n_samples >= n_fft ? (n_samples - n_fft) / hop + 1 : 0;
+  for (int i = 0; i < n_if; ++i)
+    for (int64_t s = 0; s < n_seg; ++s)
+      for (int64_t n = s * hop; n < s * hop + n_fft; ++n) {
+        const uint32_t code = (packed[i][n / per_word] >> (uint32_t)((n % per_word) * bits)) & mask;
+        counts[(size_t)i * nc + code] += 1;
+      }
+  return OR_OK;
+}
+
+/* erfc(x) = p for p in (0, 1]: bisection on [0, 40] (erfc decreasing), to the last bit. */
+static double erfc_inverse_bisect(double p) {
+  double lo = 0.0, hi = 40.0;
+  for (int it = 0; it < 2000 && hi > lo; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (erfc(mid) > p) lo = mid;
+    else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* Total power from one IF's histogram (our reading of the bit-distribution method):
+ *   moment2 = mean of level^2 over the samples (levels as decoded, step 1);
+ *   sigma_over_threshold (2-bit): a zero-mean Gaussian of rms sigma falls beyond the
+ *   sampler thresholds +-v0 with probability p = erfc(v0 / (sigma sqrt 2)); with p the
+ *   fraction of the outer codes (levels -3 and +3), sigma / v0 = 1 / (sqrt2 erfc^-1(p)).
+ *   NaN for other widths or p in {0, 1}. */
+int oracle_power(int bits, const uint64_t* counts, double* moment2, double* sigma_over_threshold) {
+  if (!(bits == 1 || bits == 2 || bits == 4 || bits == 8) || !counts) return OR_EINVAL;
+  const int nc = 1 << bits;
+  double n = 0.0, sum2 = 0.0;
+  for (int c = 0; c < nc; ++c) {
+    const double lev = decode_one(bits, (uint32_t)c);
+    n += (double)counts[c];
+    sum2 += lev * lev * (double)counts[c];
+  }
+  if (!(n > 0.0)) return OR_EINVAL;
+  if (moment2) *moment2 = sum2 / n;
+  if (sigma_over_threshold) {
+    double sg = NAN;
+    if (bits == 2) {
+      const double p = ((double)counts[0] + (double)counts[3]) / n;
+      if (p > 0.0 && p < 1.0) sg = 1.0 / (sqrt(2.0) * erfc_inverse_bisect(p));
+    }
+    *sigma_over_threshold = sg;
+  }
+  return OR_OK;
+}

@@ -40,6 +40,9 @@ POLARIS_DECLARE(19)
 
 // (args, stream, programmatic dependent launch on the predecessor in `stream`)
 typedef cudaError_t (*phase_fn)(const BatchArgs&, cudaStream_t, bool);
+// per-IF code histograms of segments [0, nseg) of `in` (polaris_stats.cu)
+cudaError_t launch_code_hist(const SegSrc& in, int n_if, int bits, int nseg, int64_t n_fft,
+                             unsigned long long* hist, int num_sms, cudaStream_t st);
 #define POLARIS_ROW(LOGN) {run_phase1<LOGN>, run_phase2<LOGN>}
 static const phase_fn kPhases[20][2] = {
     {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr},
@@ -237,6 +240,8 @@ struct polaris_spec {
   float* d_out_autos = nullptr;
   float* d_out_cross = nullptr;
   float* d_out_stokes = nullptr;
+  int code_stats = 0;
+  unsigned long long* d_hist = nullptr;  // [n_if][2^bits] code counts (code_stats only)
   cudaEvent_t ev_h2d = nullptr;
   // two internal streams: phase 1 of batch b+1 runs beside phase 2 of batch b; the
   // slab is split into two halves used by alternate batches
@@ -354,6 +359,7 @@ static void free_all(polaris_spec* s) {
   cudaFree(s->d_out_autos);
   cudaFree(s->d_out_cross);
   cudaFree(s->d_out_stokes);
+  cudaFree(s->d_hist);
   if (s->ev_h2d) cudaEventDestroy(s->ev_h2d);
 }
 
@@ -377,6 +383,7 @@ extern "C" int spectrometer_create(const polaris_config* cfg, polaris_spec** out
     return set_err(nullptr, POLARIS_EINVAL, "unknown window kind");
   if (c.window == POLARIS_WIN_CUSTOM && !c.taps) return set_err(nullptr, POLARIS_EINVAL, "custom window needs taps");
   if (c.max_batch_segments < 0) return set_err(nullptr, POLARIS_EINVAL, "max_batch_segments must be >= 0");
+  if (c.code_stats != 0 && c.code_stats != 1) return set_err(nullptr, POLARIS_EINVAL, "code_stats must be 0 or 1");
   // correlation pairs
   int pairs[2 * kMaxIF];
   int n_pair = 0;
@@ -474,8 +481,9 @@ extern "C" int spectrometer_create(const polaris_config* cfg, polaris_spec** out
   const size_t bytes_carry = (size_t)c.n_if * s->carry_words_cap * 4;
   const size_t bytes_stage = (size_t)c.n_if * s->stage_words_cap * 4;
   const size_t bytes_out = (size_t)s->nbin * 4 * (c.n_if + 2 * n_pair + 4 * n_pair);
+  const size_t bytes_hist = c.code_stats ? (size_t)c.n_if * ((size_t)1 << c.bits) * 8 : 0;
   const size_t total = acc_bytes + bytes_tw + bytes_scratch + 2 * bytes_carry + bytes_stage + bytes_out +
-                       (c.window != POLARIS_WIN_RECT ? N * 4 : 0);
+                       bytes_hist + (c.window != POLARIS_WIN_RECT ? N * 4 : 0);
   if (g_alloc_limit >= 0 && (int64_t)total > g_alloc_limit) {
     delete s;
     return set_err(nullptr, POLARIS_ENOMEM, "device allocation of %zu bytes exceeds the limit %lld", total,
@@ -492,6 +500,7 @@ extern "C" int spectrometer_create(const polaris_config* cfg, polaris_spec** out
             alloc((void**)&s->d_out_cross, (size_t)s->nbin * 8 * (n_pair ? n_pair : 1)) &&
             alloc((void**)&s->d_out_stokes, (size_t)s->nbin * 16 * (n_pair ? n_pair : 1));
   if (ok && c.window != POLARIS_WIN_RECT) ok = alloc((void**)&s->d_taps, N * 4);
+  if (ok && c.code_stats) ok = alloc((void**)&s->d_hist, bytes_hist);
   if (!ok) {
     cudaGetLastError();
     free_all(s);
@@ -515,6 +524,8 @@ extern "C" int spectrometer_create(const polaris_config* cfg, polaris_spec** out
     e = cudaMemcpy(s->d_taps, taps.data(), N * 4, cudaMemcpyHostToDevice);
   }
   if (e == cudaSuccess) e = cudaMemset(s->d_acc, 0, acc_bytes);
+  if (e == cudaSuccess && c.code_stats) e = cudaMemset(s->d_hist, 0, bytes_hist);
+  s->code_stats = c.code_stats;
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_h2d, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st_p1, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st_p2, cudaStreamNonBlocking);
@@ -629,6 +640,12 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
   a.bits = s->bits;
   a.num_sms = s->num_sms;
   const phase_fn f1 = kPhases[s->logn][0], f2 = kPhases[s->logn][1];
+  if (nseg > 0 && s->code_stats) {
+    cudaError_t e = counted_launch(s, 3, st, [&]() {
+      return launch_code_hist(a.in, s->n_if, s->bits, (int)nseg, N, s->d_hist, s->num_sms, st);
+    });
+    if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "code-histogram launch: %s", cudaGetErrorString(e));
+  }
   if (nseg > 0 && nseg <= s->max_batch) {
     // one pass: both phases on the caller's stream, each a programmatic dependent launch
     // (its CTAs set up while the previous kernel drains, then wait for it) unless launches
@@ -832,10 +849,25 @@ extern "C" int spectrometer_kernel_times(polaris_spec* s, double* ms, int64_t* l
     CUDA_OR_FAIL(s, cudaEventSynchronize(r.b));
     float t = 0.f;
     CUDA_OR_FAIL(s, cudaEventElapsedTime(&t, r.a, r.b));
-    ms[r.kind] += t;
-    launches[r.kind] += 1;
+    if (r.kind < n) {
+      ms[r.kind] += t;
+      launches[r.kind] += 1;
+    }
   }
   drop_prof(s);
+  return POLARIS_OK;
+}
+
+extern "C" int spectrometer_code_histogram(polaris_spec* s, uint64_t* counts, int reset) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (!counts) return set_err(s, POLARIS_EINVAL, "null counts");
+  if (!s->code_stats) return set_err(s, POLARIS_ESTATE, "spectrometer created with code_stats = 0");
+  DeviceGuard dg(s->device);
+  const size_t bytes = (size_t)s->n_if * ((size_t)1 << s->bits) * 8;
+  CUDA_OR_FAIL(s, cudaDeviceSynchronize());  // the counts of everything queued so far
+  CUDA_OR_FAIL(s, cudaMemcpy(counts, s->d_hist, bytes, cudaMemcpyDeviceToHost));
+  if (reset) CUDA_OR_FAIL(s, cudaMemset(s->d_hist, 0, bytes));
   return POLARIS_OK;
 }
 

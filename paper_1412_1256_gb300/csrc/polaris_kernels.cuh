@@ -817,8 +817,11 @@ cudaError_t run_phase2(const BatchArgs& a, cudaStream_t st, bool pdl) {
   const long long warps = (long long)per_sm * a.num_sms * PL::WARPS;
   const int R = (a.nseg + PL::SL - 1) / PL::SL;
   const long long groups = (long long)a.n_fpair * PL::UGW;
-  long long range_len = (groups * R + warps - 1) / warps;  // rounds per item
-  if (range_len < 1) range_len = 1;
+  // as many segment ranges per (pair, unit group) as leave every warp at most one item
+  long long nrg = warps / groups;
+  if (nrg < 1) nrg = 1;
+  if (nrg > R) nrg = R;
+  const long long range_len = (R + nrg - 1) / nrg;  // rounds per item
   const long long n_items = groups * ((R + range_len - 1) / range_len);
   const long long ctas = (n_items + PL::WARPS - 1) / PL::WARPS;
   const long long cap = (long long)per_sm * a.num_sms;

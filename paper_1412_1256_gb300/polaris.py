@@ -28,6 +28,7 @@ EXPORTS = (
     "spectrometer_n_bins", "spectrometer_n_pairs", "spectrometer_debug_unpack", "spectrometer_destroy",
     "spectrometer_last_error", "polaris_set_alloc_limit", "spectrometer_kernel_launches",
     "spectrometer_set_profiling", "spectrometer_kernel_times", "spectrometer_run_noalloc",
+    "spectrometer_code_histogram", "polaris_power_from_histogram",
 )
 
 
@@ -42,7 +43,7 @@ class polaris_config(ctypes.Structure):
         ("n_if", ctypes.c_int), ("bits", ctypes.c_int), ("n_fft", ctypes.c_int64), ("hop", ctypes.c_int64),
         ("window", ctypes.c_int), ("taps", ctypes.POINTER(ctypes.c_float)), ("n_pair", ctypes.c_int),
         ("pairs", ctypes.POINTER(ctypes.c_int)), ("accum_fp64", ctypes.c_int), ("device", ctypes.c_int),
-        ("max_batch_segments", ctypes.c_int),
+        ("max_batch_segments", ctypes.c_int), ("code_stats", ctypes.c_int),
     ]
 
 
@@ -95,6 +96,11 @@ def load(path: str = LIB_PATH):
             lib.spectrometer_run_noalloc.restype = ci
             lib.polaris_set_alloc_limit.argtypes = [i64]
             lib.polaris_set_alloc_limit.restype = None
+            lib.spectrometer_code_histogram.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ci]
+            lib.spectrometer_code_histogram.restype = ci
+            lib.polaris_power_from_histogram.argtypes = [ci, ctypes.POINTER(ctypes.c_uint64),
+                                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+            lib.polaris_power_from_histogram.restype = ci
             _lib = lib
     return _lib
 
@@ -118,11 +124,23 @@ def _ptr(x):
     return int(x.data_ptr())
 
 
+def power_from_histogram(bits: int, counts) -> tuple[float, float]:
+    """(moment2, sigma_over_threshold) of one IF's code histogram (polaris_power_from_histogram)."""
+    c = np.ascontiguousarray(np.asarray(counts, dtype=np.uint64).reshape(-1))
+    m2, sg = ctypes.c_double(), ctypes.c_double()
+    rc = load().polaris_power_from_histogram(int(bits), c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                             ctypes.byref(m2), ctypes.byref(sg))
+    if rc != OK:
+        raise PolarisError(rc, "invalid histogram")
+    return m2.value, sg.value
+
+
 class Spectrometer:
     """One spectrometer handle.  Mirrors spectrometer_create / feed / integrate / destroy."""
 
     def __init__(self, n_if: int, bits: int, n_fft: int, hop: int = 0, window="rect", pairs=None,
-                 accum_fp64: bool = False, device: int = 0, max_batch_segments: int = 0):
+                 accum_fp64: bool = False, device: int = 0, max_batch_segments: int = 0,
+                 code_stats: bool = False):
         lib = load()
         cfg = polaris_config()
         cfg.n_if, cfg.bits, cfg.n_fft, cfg.hop = n_if, bits, n_fft, hop
@@ -143,6 +161,7 @@ class Spectrometer:
         cfg.accum_fp64 = int(bool(accum_fp64))
         cfg.device = device
         cfg.max_batch_segments = max_batch_segments
+        cfg.code_stats = int(bool(code_stats))
         h = ctypes.c_void_p()
         rc = lib.spectrometer_create(ctypes.byref(cfg), ctypes.byref(h))
         if rc != OK:
@@ -246,14 +265,23 @@ class Spectrometer:
     def set_profiling(self, on: bool) -> None:
         self._check(load().spectrometer_set_profiling(self._h, int(bool(on))))
 
-    KERNEL_KINDS = ("phase1_decode_rowdft", "phase2_coldft_correlate", "readout_stokes")
+    KERNEL_KINDS = ("phase1_decode_rowdft", "phase2_coldft_correlate", "readout_stokes", "code_histogram")
 
     def kernel_times(self):
         """{kind: (total_ms, launches)} for launches bracketed since set_profiling(True)."""
-        ms = (ctypes.c_double * 3)()
-        nl = (ctypes.c_int64 * 3)()
-        self._check(load().spectrometer_kernel_times(self._h, ms, nl, 3))
+        n = len(self.KERNEL_KINDS)
+        ms = (ctypes.c_double * n)()
+        nl = (ctypes.c_int64 * n)()
+        self._check(load().spectrometer_kernel_times(self._h, ms, nl, n))
         return {k: (ms[i], int(nl[i])) for i, k in enumerate(self.KERNEL_KINDS)}
+
+    def code_histogram(self, reset: bool = False) -> np.ndarray:
+        """Per-IF code counts [n_if, 2^bits] (uint64) over the segments integrated since creation
+        or the last reset (needs code_stats=True)."""
+        out = np.zeros((self.n_if, 1 << self.bits), np.uint64)
+        self._check(load().spectrometer_code_histogram(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                                       int(bool(reset))))
+        return out
 
     def debug_unpack(self, words: np.ndarray, n: int) -> np.ndarray:
         w = np.ascontiguousarray(words, dtype=np.uint32)
