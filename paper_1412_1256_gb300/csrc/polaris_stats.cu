@@ -49,33 +49,45 @@ __device__ __forceinline__ void count_word(uint32_t w, uint32_t (&c)[(BITS <= 4)
 
 // grid (x: word blocks, y: IF); every word of every segment of the IF once.  Counts are
 // summed in registers, then over the block in shared memory, so that each block adds
-// one value per code to the global histogram (few blocks per IF: the global atomics all
-// hit the same 2^b addresses).
+// one value per code to the global histogram (few, wide blocks per IF: the global
+// atomics all hit the same 2^b addresses).
+constexpr int kHistThreads = 512, kHistWords = 16;  // words per thread per pass, all loads in flight
+
 template <int BITS>
-__global__ void __launch_bounds__(256) k_code_hist(HistArgs a) {
-  constexpr int NC = 1 << BITS, NR = (BITS <= 4) ? NC : 1;
-  __shared__ uint32_t sh[NC * (BITS == 8 ? 1 : 8)];  // 8-bit: the block's bins; else [warp][code]
+__global__ void __launch_bounds__(kHistThreads, 2) k_code_hist(HistArgs a) {
+  constexpr int NC = 1 << BITS, NR = (BITS <= 4) ? NC : 1, NW = kHistThreads / 32;
+  __shared__ uint32_t sh[NC * (BITS == 8 ? 1 : NW)];  // 8-bit: the block's bins; else [warp][code]
   const int ifx = blockIdx.y, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   uint32_t c[NR];
 #pragma unroll
   for (int v = 0; v < NR; ++v) c[v] = 0;
   if constexpr (BITS == 8) {
-    for (int v = threadIdx.x; v < NC; v += blockDim.x) sh[v] = 0;
+    for (int v = threadIdx.x; v < NC; v += kHistThreads) sh[v] = 0;
     __syncthreads();
   }
   const long long total = (long long)a.nseg << a.wps_log2;
   const long long wmask = (1LL << a.wps_log2) - 1;
-  const long long stride = (long long)gridDim.x * blockDim.x;
   // this IF's two sources (staged segments [0, n0), then the caller's input)
   const uint32_t* src0 = a.in.src0[ifx];
   const uint32_t* src1 = a.in.src1[ifx];
   const long long hop_w = a.in.hop_w;
   const int n0 = a.in.n0;
-#pragma unroll 4
-  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += stride) {
-    const int s = (int)(k >> a.wps_log2);
-    const uint32_t* p = (s < n0 ? src0 + s * hop_w : src1 + (s - n0) * hop_w) + (k & wmask);
-    count_word<BITS>(__ldg(p), c, sh);
+  const long long chunk = (long long)kHistThreads * kHistWords;
+  for (long long base = (long long)blockIdx.x * chunk; base < total; base += (long long)gridDim.x * chunk) {
+    uint32_t w[kHistWords];
+#pragma unroll
+    for (int j = 0; j < kHistWords; ++j) {  // coalesced: consecutive threads, consecutive words
+      const long long k = base + (long long)j * kHistThreads + threadIdx.x;
+      w[j] = 0;
+      if (k < total) {
+        const int s = (int)(k >> a.wps_log2);
+        w[j] = __ldg((s < n0 ? src0 + s * hop_w : src1 + (s - n0) * hop_w) + (k & wmask));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < kHistWords; ++j) {
+      if (base + (long long)j * kHistThreads + threadIdx.x < total) count_word<BITS>(w[j], c, sh);
+    }
   }
   unsigned long long* h = a.hist + (size_t)ifx * NC;
   if constexpr (BITS <= 4) {
@@ -87,14 +99,14 @@ __global__ void __launch_bounds__(256) k_code_hist(HistArgs a) {
       if (lane == 0) sh[warp * NC + v] = x;
     }
     __syncthreads();
-    for (int v = threadIdx.x; v < NC; v += blockDim.x) {
+    for (int v = threadIdx.x; v < NC; v += kHistThreads) {
       unsigned long long t = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w * NC + v];
+      for (int q = 0; q < NW; ++q) t += sh[q * NC + v];
       if (t) atomicAdd(h + v, t);
     }
   } else {
     __syncthreads();
-    for (int v = threadIdx.x; v < NC; v += blockDim.x)
+    for (int v = threadIdx.x; v < NC; v += kHistThreads)
       if (sh[v]) atomicAdd(h + v, (unsigned long long)sh[v]);
   }
 }
@@ -110,17 +122,17 @@ cudaError_t launch_code_hist(const SegSrc& in, int n_if, int bits, int nseg, int
   a.wps_log2 = wl;
   a.hist = hist;
   const long long total = (long long)nseg << wl;
-  // about 32 words per thread, at most 2 blocks per SM over all IFs
-  long long bx = (total + 256LL * 32 - 1) / (256LL * 32);
-  const long long cap = (2LL * num_sms + n_if - 1) / n_if;
+  const long long chunk = (long long)kHistThreads * kHistWords;
+  long long bx = (total + chunk - 1) / chunk;                 // one pass per block where possible
+  const long long cap = (2LL * num_sms + n_if - 1) / n_if;  // at most two blocks per SM over all IFs
   if (bx > cap) bx = cap;
   if (bx < 1) bx = 1;
   const dim3 grid((unsigned)bx, (unsigned)n_if);
   switch (bits) {
-    case 1: k_code_hist<1><<<grid, 256, 0, st>>>(a); break;
-    case 2: k_code_hist<2><<<grid, 256, 0, st>>>(a); break;
-    case 4: k_code_hist<4><<<grid, 256, 0, st>>>(a); break;
-    case 8: k_code_hist<8><<<grid, 256, 0, st>>>(a); break;
+    case 1: k_code_hist<1><<<grid, kHistThreads, 0, st>>>(a); break;
+    case 2: k_code_hist<2><<<grid, kHistThreads, 0, st>>>(a); break;
+    case 4: k_code_hist<4><<<grid, kHistThreads, 0, st>>>(a); break;
+    case 8: k_code_hist<8><<<grid, kHistThreads, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
