@@ -171,6 +171,24 @@ __device__ __forceinline__ float decode_level(uint32_t word, uint32_t shift) {
   }
 }
 
+// The same decode from a rotation of the word, for a lane that decodes the same bit
+// offset of many words: with rot = decode_rot<BITS>(shift) computed once, a code sits at
+// bits [1, BITS] (b < 8) or [0, 8) (b = 8) of rotr(word, rot), so one funnel shift, one
+// three-input logic op and one add give the level.
+template <int BITS>
+__host__ __device__ constexpr uint32_t decode_rot(uint32_t shift) {
+  return BITS == 8 ? shift : ((shift + 31u) & 31u);
+}
+template <int BITS>
+__device__ __forceinline__ float decode_level_rot(uint32_t word, uint32_t rot) {
+  const uint32_t r = __funnelshift_r(word, word, rot);
+  if constexpr (BITS == 8) {
+    return __uint_as_float((r & 0xFFu) ^ 0x4B000080u) - 8388736.0f;  // 2^23 + (c ^ 0x80) - 2^23 - 128
+  } else {
+    return __uint_as_float((r & (((1u << BITS) - 1u) << 1)) | 0x4B000000u) - (8388608.0f + (float)((1 << BITS) - 1));
+  }
+}
+
 // ----------------------------------------------------------------------------------------
 // two-phase plan: N = N1 * N2, n = N2 a + b (a row, b column), k = c + N1 d
 //   phase 1: for each column b, DFT-N1 over a (P points per thread, Q1 = N1/P threads)

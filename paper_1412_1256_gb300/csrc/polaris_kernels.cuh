@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
         const int col = (it * PL::WARPS + warp) * CW + cw;  // column inside the tile
         const long long b = b0 + col;
         const int wd = (col * BITS) >> 5;
-        const uint32_t shift = (uint32_t)((col * BITS) & 31);
+        const uint32_t rot = decode_rot<BITS>((uint32_t)((col * BITS) & 31));
         const uint32_t* sb = stage + buf * SB + 2 * wd;
         float2 v[P];
         // decode the lane's 32 rows; the pair's shape and the window are uniform per tile
@@ -427,8 +427,8 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
             constexpr int t = decltype(t_)::value;
             const int row = q1 + Q1 * t;
             const uint2 w = *reinterpret_cast<const uint2*>(sb + row * RS);  // IF a, IF b
-            float x = decode_level<BITS>(w.x, shift);
-            float y = HB ? decode_level<BITS>(w.y, shift) : 0.0f;
+            float x = decode_level_rot<BITS>(w.x, rot);
+            float y = HB ? decode_level_rot<BITS>(w.y, rot) : 0.0f;
             if constexpr (TP) {
               const float tv = __ldg(a.taps + row * N2 + b);
               x *= tv;
