@@ -47,7 +47,7 @@ enum {
   POLARIS_ECUDA = -3,    /* a CUDA call failed; the handle is now unusable   */
   POLARIS_ESTATE = -4,   /* wrong state (e.g. integrate with zero segments,
                             or a handle after a CUDA error)                  */
-  POLARIS_ETIMEOUT = -5  /* reserved for bounded device-side waits           */
+  POLARIS_ETIMEOUT = -5  /* a bounded device-side wait ran out (see below)   */
 };
 
 /* window kinds (Sec. 3.1: rectangular online; Sec. 5: others possible) */
@@ -221,6 +221,18 @@ int spectrometer_code_histogram(polaris_spec* s, uint64_t* counts, int reset);
  * Either output pointer may be NULL.  Returns POLARIS_EINVAL for a bad width, NULL
  * counts or an empty histogram. */
 int polaris_power_from_histogram(int bits, const uint64_t* counts, double* moment2, double* sigma_over_threshold);
+
+/* Bounded device-side waits.  Phase 2 (N >= 2^17) prefetches its next columns with
+ * asynchronous bulk copies and waits for them on a shared-memory barrier; every such wait
+ * polls at most a fixed number of times.  If one runs out, the kernel records the fact in
+ * the handle's device status word, waits (again bounded) for its own copies in flight,
+ * releases its tensor memory and returns; the readout then writes NaN to every output,
+ * and the next synchronising call on the handle (spectrometer_integrate,
+ * spectrometer_code_histogram) returns POLARIS_ETIMEOUT, after which the handle is
+ * unusable (POLARIS_ESTATE).  The GPU context stays usable.
+ * Test hook: polls per wait for later launches (0 makes every such wait run out at once;
+ * a negative value restores the default of 2^20). */
+void polaris_set_wait_limit(int64_t polls);
 
 /* Test hook: cap the bytes of device memory that later spectrometer_create
  * calls may allocate (-1 = no cap), so that allocation failure can be tested

@@ -82,6 +82,7 @@ struct ReadoutArgs {
   int feed;
   float c2, s2;
   float inv_ga2[kMaxIF], inv_gb2[kMaxIF], ig_re[kMaxIF], ig_im[kMaxIF];  // 1/|Ga|^2, 1/|Gb|^2, 1/(Ga conj Gb)
+  const int* err;  // nonzero: a phase kernel gave up a wait; every output is NaN
 };
 
 // Readout of one block: TD consecutive values of d times all N1 values of c, i.e. the natural
@@ -138,6 +139,7 @@ __global__ void __launch_bounds__(kReadoutThreads) k_readout(ReadoutArgs a) {
     tile[sidx[i]] = v[i];
   }
   __syncthreads();
+  const bool failed = a.err && *a.err != 0;
   const int p = a.fcorr[f];
   float* autos_a = a.autos ? a.autos + (size_t)a.fa[f] * a.nbin : nullptr;
   float* autos_b = (a.autos && a.fb[f] >= 0) ? a.autos + (size_t)a.fb[f] * a.nbin : nullptr;
@@ -154,7 +156,11 @@ __global__ void __launch_bounds__(kReadoutThreads) k_readout(ReadoutArgs a) {
     const int k = N1 * d0 + e;
     if (k >= a.nbin) break;
     const int dd = e / N1, c = e - dd * N1;
-    const float4 v = tile[dd * (N1 + 1) + c];
+    float4 v = tile[dd * (N1 + 1) + c];
+    if (failed) {
+      const float qnan = __int_as_float(0x7fc00000);
+      v = make_float4(qnan, qnan, qnan, qnan);
+    }
     const float xx = v.x, yy = v.y, xr = v.z, xi = v.w;
     if (autos_a) autos_a[k] = xx;
     if (autos_b) autos_b[k] = yy;
@@ -242,6 +248,7 @@ struct polaris_spec {
   float* d_out_stokes = nullptr;
   int code_stats = 0;
   unsigned long long* d_hist = nullptr;  // [n_if][2^bits] code counts (code_stats only)
+  int* d_err = nullptr;                  // device status word written by the phase kernels
   cudaEvent_t ev_h2d = nullptr;
   // two internal streams: phase 1 of batch b+1 runs beside phase 2 of batch b; the
   // slab is split into two halves used by alternate batches
@@ -360,10 +367,18 @@ static void free_all(polaris_spec* s) {
   cudaFree(s->d_out_cross);
   cudaFree(s->d_out_stokes);
   cudaFree(s->d_hist);
+  cudaFree(s->d_err);
   if (s->ev_h2d) cudaEventDestroy(s->ev_h2d);
 }
 
 extern "C" void polaris_set_alloc_limit(int64_t bytes) { g_alloc_limit = bytes; }
+
+// polls of a bounded device-side wait before it counts as timed out (test hook below)
+static constexpr unsigned kDefaultWaitLimit = 1u << 20;
+static unsigned g_wait_limit = kDefaultWaitLimit;
+extern "C" void polaris_set_wait_limit(int64_t polls) {
+  g_wait_limit = polls < 0 ? kDefaultWaitLimit : (polls > 0x7fffffff ? 0x7fffffffu : (unsigned)polls);
+}
 
 extern "C" int spectrometer_create(const polaris_config* cfg, polaris_spec** out) {
   if (!cfg || !out) return set_err(nullptr, POLARIS_EINVAL, "null config or output pointer");
@@ -501,6 +516,7 @@ extern "C" int spectrometer_create(const polaris_config* cfg, polaris_spec** out
             alloc((void**)&s->d_out_stokes, (size_t)s->nbin * 16 * (n_pair ? n_pair : 1));
   if (ok && c.window != POLARIS_WIN_RECT) ok = alloc((void**)&s->d_taps, N * 4);
   if (ok && c.code_stats) ok = alloc((void**)&s->d_hist, bytes_hist);
+  if (ok) ok = alloc((void**)&s->d_err, 256);
   if (!ok) {
     cudaGetLastError();
     free_all(s);
@@ -525,6 +541,7 @@ extern "C" int spectrometer_create(const polaris_config* cfg, polaris_spec** out
   }
   if (e == cudaSuccess) e = cudaMemset(s->d_acc, 0, acc_bytes);
   if (e == cudaSuccess && c.code_stats) e = cudaMemset(s->d_hist, 0, bytes_hist);
+  if (e == cudaSuccess) e = cudaMemset(s->d_err, 0, 256);
   s->code_stats = c.code_stats;
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_h2d, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->st_p1, cudaStreamNonBlocking);
@@ -561,6 +578,23 @@ extern "C" int spectrometer_n_pairs(const polaris_spec* s) { return s ? s->n_pai
 static int check_usable(polaris_spec* s) {
   if (!s) return POLARIS_EINVAL;
   if (s->broken) return set_err(s, POLARIS_ESTATE, "handle unusable after an earlier CUDA error: %s", s->err.c_str());
+  return POLARIS_OK;
+}
+
+// After a synchronisation: a phase kernel that gave up a bounded wait has set the status
+// word (its outputs are NaN); the handle becomes unusable.
+static int check_device_status(polaris_spec* s) {
+  int st = 0;
+  const cudaError_t e = cudaMemcpy(&st, s->d_err, sizeof st, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    s->broken = true;
+    return set_err(s, POLARIS_ECUDA, "status read: %s", cudaGetErrorString(e));
+  }
+  if (st) {
+    set_err(s, POLARIS_ETIMEOUT, "a device-side wait ran out of its bound; outputs are NaN");
+    s->broken = true;
+    return POLARIS_ETIMEOUT;
+  }
   return POLARIS_OK;
 }
 
@@ -639,6 +673,8 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
   a.fp64 = s->accum_fp64;
   a.bits = s->bits;
   a.num_sms = s->num_sms;
+  a.err = s->d_err;
+  a.wait_limit = g_wait_limit;
   const phase_fn f1 = kPhases[s->logn][0], f2 = kPhases[s->logn][1];
   if (nseg > 0 && s->code_stats) {
     cudaError_t e = counted_launch(s, 3, st, [&]() {
@@ -709,6 +745,7 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
 static int fill_readout(polaris_spec* s, const polaris_stokes_params* prm, ReadoutArgs& r) {
   memset(&r, 0, sizeof r);
   r.acc = s->d_acc;
+  r.err = s->d_err;
   r.fp64 = s->accum_fp64;
   r.N1 = s->N1;
   r.N2 = s->N2;
@@ -789,7 +826,7 @@ extern "C" int spectrometer_integrate(polaris_spec* s, const polaris_stokes_para
     CUDA_OR_FAIL(s, cudaMemcpyAsync(stokes, s->d_out_stokes, (size_t)s->nbin * 16 * s->n_pair,
                                     cudaMemcpyDeviceToHost, nullptr));
   CUDA_OR_FAIL(s, cudaStreamSynchronize(nullptr));
-  return POLARIS_OK;
+  return check_device_status(s);
 }
 
 extern "C" int spectrometer_debug_unpack(polaris_spec* s, const void* packed, int64_t n, float* out) {
@@ -866,6 +903,8 @@ extern "C" int spectrometer_code_histogram(polaris_spec* s, uint64_t* counts, in
   DeviceGuard dg(s->device);
   const size_t bytes = (size_t)s->n_if * ((size_t)1 << s->bits) * 8;
   CUDA_OR_FAIL(s, cudaDeviceSynchronize());  // the counts of everything queued so far
+  rc = check_device_status(s);
+  if (rc) return rc;
   CUDA_OR_FAIL(s, cudaMemcpy(counts, s->d_hist, bytes, cudaMemcpyDeviceToHost));
   if (reset) CUDA_OR_FAIL(s, cudaMemset(s->d_hist, 0, bytes));
   return POLARIS_OK;
@@ -983,8 +1022,9 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
   const size_t acc_bytes = align256((size_t)nf * native * 4 * (c.accum_fp64 ? 8 : 4));
   const size_t tw_bytes = align256((size_t)N2 * (UPS + 1) * sizeof(float2));
   const size_t taps_bytes = c.window == POLARIS_WIN_RECT ? 0 : align256((size_t)N * 4);
+  const size_t err_bytes = 256;  // the phase kernels' status word
   const size_t per_seg = (size_t)nf * N * sizeof(float2);
-  const size_t fixed = acc_bytes + tw_bytes + taps_bytes;
+  const size_t fixed = acc_bytes + tw_bytes + taps_bytes + err_bytes;
   if (fixed + per_seg > POLARIS_NOALLOC_BYTES)
     return set_err(nullptr, POLARIS_EINVAL,
                    "configuration needs %zu bytes of scratch for one segment, above the %u-byte static limit",
@@ -1011,11 +1051,13 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
   void* acc = base;
   float2* tw = reinterpret_cast<float2*>(base + acc_bytes);
   float* taps = c.window == POLARIS_WIN_RECT ? nullptr : reinterpret_cast<float*>(base + acc_bytes + tw_bytes);
+  int* d_err = reinterpret_cast<int*>(base + acc_bytes + tw_bytes + taps_bytes);
   float2* slab = reinterpret_cast<float2*>(base + fixed);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   int num_sms = 0;
   cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, c.device);
   cudaError_t e = cudaMemsetAsync(acc, 0, acc_bytes, st);  // accumulators start at zero
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, sizeof(int), st);
   if (e == cudaSuccess) {
     const long long ntw = (long long)N2 * (UPS + 1);
     k_noalloc_twiddles<<<(unsigned)((ntw + 255) / 256), 256, 0, st>>>(tw, N2, UPS, N);
@@ -1044,6 +1086,8 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
   a.n_fpair = nf;
   a.taps = taps;
   a.scratch = slab;
+  a.err = d_err;
+  a.wait_limit = g_wait_limit;
   a.tw = tw;
   a.acc = acc;
   a.fp64 = c.accum_fp64 ? 1 : 0;
@@ -1059,6 +1103,7 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
   ReadoutArgs r;
   memset(&r, 0, sizeof r);
   r.acc = acc;
+  r.err = d_err;
   r.fp64 = a.fp64;
   r.N1 = N1;
   r.N2 = N2;

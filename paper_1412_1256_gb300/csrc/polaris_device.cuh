@@ -320,7 +320,11 @@ struct Plan {
   static constexpr int TACC = ((2 * P + 15) / 16) * 16;    // tensor-memory columns per lane: accumulators
   static constexpr int TTW = ((2 * P + 15) / 16) * 16;     // and the lane's column twiddles W_N^{b u}
   static constexpr int TCOLS2 = pow2_at_least((WARPS / 4) * (TACC + TTW), 32);
-  static constexpr size_t SMEM2 = sizeof(float2) * ((size_t)WARPS * REGION2 + TWT) + 16;
+  // phase 2 prefetches the next segment's two columns into the warp's region with bulk
+  // copies when a warp holds one unit of 16-lane columns (N2 = 512: 2^17 and up)
+  static constexpr bool PF2 = (SL == 1) && (UPW == 1) && (Q2 == 16);
+  // regions | W_N2 table | tensor-memory slot (16 B) | one mbarrier per warp
+  static constexpr size_t SMEM2 = sizeof(float2) * ((size_t)WARPS * REGION2 + TWT) + 16 + 8 * WARPS;
 
   static_assert(N1 * N2 == N, "plan");
   static_assert(Q1 >= 1 && Q1 <= 32 && P1 % Q1 == 0 && Q2 >= 1 && 2 * Q2 <= P && 16 % Q2 == 0, "plan bounds");

@@ -67,12 +67,14 @@ struct BatchArgs {
   int seg0;             // first feed segment of this batch
   int nseg;             // segments in this batch
   const float* taps;    // window taps (N) or nullptr for the rectangular window
-  float2* scratch;      // [nseg * n_fpair][N2][N1]
+  float2* scratch;      // slab [nseg * n_fpair][N1][N2]: row c (phase-1 output index), b contiguous
   const float2* tw;     // [N2][UPS + 1]: W_N^{b u}
   void* acc;            // native accumulators [n_fpair][N/2 + 1] of float4 (or double4 if fp64)
   int fp64;
   int bits;
   int num_sms;
+  int* err;             // device status word: set to 1 when a bounded wait ran out (see k_phase2)
+  unsigned wait_limit;  // iterations of a bounded mbarrier wait before it counts as timed out
 };
 
 __device__ __forceinline__ const uint32_t* seg_ptr(const SegSrc& in, int ifx, int s) {
@@ -100,6 +102,38 @@ __device__ __forceinline__ void tma_store_2d_elect(const CUtensorMap* map, const
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+// mbarrier + bulk copies (phase-2 prefetch): one barrier per warp, expected-transaction
+// counting; every wait is bounded by an iteration count
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+// one elected lane of the converged warp: announce `bytes`, then copy two contiguous blocks
+// global -> shared, both completing on `bar`
+__device__ __forceinline__ void bulk_load2_elect(uint32_t bar, uint32_t dst0, const void* src0, uint32_t dst1,
+                                                 const void* src1, uint32_t bytes_each) {
+  asm volatile(
+      "{\n .reg .pred p;\n .reg .b32 r;\n elect.sync r|p, 0xffffffff;\n"
+      " @p mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %5;\n"
+      " @p cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%1], [%2], %6, [%0];\n"
+      " @p cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%3], [%4], %6, [%0];\n}\n" ::"r"(bar),
+      "r"(dst0), "l"(src0), "r"(dst1), "l"(src1), "r"(2 * bytes_each), "r"(bytes_each)
+      : "memory");
+}
+// true once the barrier's phase `parity` has completed; false after `limit` polls
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0; i < limit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (__any_sync(0xffffffffu, done != 0)) return true;  // phases only move forward
+  }
+  return false;
+}
+constexpr uint32_t kWaitAfterTimeout = 1u << 24;  // second, fixed bound: copies in flight land
+
 // programmatic dependent launch: a kernel launched with programmatic stream serialisation may
 // start before its predecessor in the stream ends; pdl_wait() returns once the predecessor
 // has completed and its memory operations are visible (at once for an ordinary launch).
@@ -482,6 +516,23 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
   float2* region = sm2 + warp * PL::REGION2;
   float2* tw2 = sm2 + PL::WARPS * PL::REGION2;  // skewed table: W_N2^k at k + k/32
   uint32_t* tslot = reinterpret_cast<uint32_t*>(tw2 + PL::TWT);
+  // prefetch (PF): the next segment's two columns arrive in the warp's region by bulk copy
+  constexpr bool PF = PL::PF2;
+  const uint32_t bar = smem_addr(reinterpret_cast<uint64_t*>(tslot + 4) + warp);
+  if constexpr (PF) {
+    if (lane == 0) mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    fence_async_shared();
+    __syncwarp();
+  }
+  uint32_t parity = 0;
+  bool stop = false;  // a bounded wait ran out: no further work, no flush
+  auto prefetch = [&](int f_, int u_, int s_) {
+    const float2* col = a.scratch + ((size_t)s_ * a.n_fpair + f_) * N1 * N2;
+    const int c0 = (u_ == 0) ? 0 : u_, c1 = (u_ == 0) ? N1 / 2 : N1 - u_;
+    bulk_load2_elect(bar, smem_addr(region), col + (size_t)c0 * N2, smem_addr(region + N2), col + (size_t)c1 * N2,
+                     (uint32_t)(N2 * sizeof(float2)));
+  };
 
   // lane roles: step 1 (uw, e, q2); step 2 (uw, j)
   const int uw = lane / (2 * Q2), e1 = (lane / Q2) & 1, q2 = lane % Q2, j = lane % (2 * Q2);
@@ -532,17 +583,49 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
     float extra[4] = {0.f, 0.f, 0.f, 0.f};
     bool worked = false;
     const int r_end = min(R, (rg + 1) * range_len);
+    if constexpr (PF) {
+      if (rg * range_len < r_end) {
+        fence_async_shared();  // the previous item's shared reads of the region come first
+        __syncwarp();
+        prefetch(f, u, rg * range_len);
+      }
+    }
+    // after the region is free: start the next segment's copy
+    auto next_prefetch = [&](int rnd_) {
+      if constexpr (PF) {
+        if (rnd_ + 1 < r_end) {
+          fence_async_shared();  // this warp's shared reads before the copy's writes
+          __syncwarp();
+          prefetch(f, u, rnd_ + 1);
+        }
+      }
+    };
     for (int rnd = rg * range_len; rnd < r_end; ++rnd) {
       const int s = rnd * SL + so;
       const bool act = s < a.nseg;
       worked |= act;
       // step 1: load the column, twiddle, P-point DFT
-      const float2* src = a.scratch + ((size_t)(act ? s : 0) * a.n_fpair + f) * N1 * N2 + (size_t)c * N2 + q2;
       float2 v[P];
-      sfor<0, P>([&](auto t_) {
-        constexpr int t = decltype(t_)::value;
-        v[ct::bitrev(t, P)] = act ? __ldcg(src + Q2 * t) : make_float2(0.f, 0.f);
-      });
+      if constexpr (PF) {
+        if (!mbar_wait_bounded(bar, parity, a.wait_limit)) {
+          if (lane == 0 && a.err) atomicExch(a.err, 1);
+          mbar_wait_bounded(bar, parity, kWaitAfterTimeout);  // the copy in flight lands first
+          stop = true;
+        }
+        parity ^= 1u;
+        if (stop) break;
+        sfor<0, P>([&](auto t_) {
+          constexpr int t = decltype(t_)::value;
+          v[ct::bitrev(t, P)] = region[e1 * N2 + q2 + Q2 * t];
+        });
+        __syncwarp();  // every lane has its column before the transpose overwrites the region
+      } else {
+        const float2* src = a.scratch + ((size_t)(act ? s : 0) * a.n_fpair + f) * N1 * N2 + (size_t)c * N2 + q2;
+        sfor<0, P>([&](auto t_) {
+          constexpr int t = decltype(t_)::value;
+          v[ct::bitrev(t, P)] = act ? __ldcg(src + Q2 * t) : make_float2(0.f, 0.f);
+        });
+      }
       sfor<0, (P + 7) / 8>([&](auto c_) {
         constexpr int cc = decltype(c_)::value;
         float w16[16];
@@ -588,6 +671,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
         });
       });
       __syncwarp();  // region consumed
+      if (!warp_special) next_prefetch(rnd);
       float2* s0 = region + (uw * 2 + 0) * N2;  // unit 0 mirror exchange: column 0
       float2* sh = region + (uw * 2 + 1) * N2;  //                         column N1/2
       if (warp_special) {
@@ -644,8 +728,12 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
         const float2 t = sh[N2 / 2];
         corr_acc(extra, sh[N2 / 2 - 1], make_float2(t.x, -t.y));
       }
-      if (warp_special) __syncwarp();  // mirror area read before the next transpose
+      if (warp_special) {
+        __syncwarp();  // mirror area read before the next transpose
+        next_prefetch(rnd);
+      }
     }
+    if (stop) break;
     // flush this lane's sums into the integration accumulators (native order)
     const size_t base = (size_t)f * PL::NATIVE;
     sfor<0, (NACC + 3) / 4>([&](auto c_) {

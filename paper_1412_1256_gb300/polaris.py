@@ -28,7 +28,7 @@ EXPORTS = (
     "spectrometer_n_bins", "spectrometer_n_pairs", "spectrometer_debug_unpack", "spectrometer_destroy",
     "spectrometer_last_error", "polaris_set_alloc_limit", "spectrometer_kernel_launches",
     "spectrometer_set_profiling", "spectrometer_kernel_times", "spectrometer_run_noalloc",
-    "spectrometer_code_histogram", "polaris_power_from_histogram",
+    "spectrometer_code_histogram", "polaris_power_from_histogram", "polaris_set_wait_limit",
 )
 
 
@@ -96,6 +96,8 @@ def load(path: str = LIB_PATH):
             lib.spectrometer_run_noalloc.restype = ci
             lib.polaris_set_alloc_limit.argtypes = [i64]
             lib.polaris_set_alloc_limit.restype = None
+            lib.polaris_set_wait_limit.argtypes = [i64]
+            lib.polaris_set_wait_limit.restype = None
             lib.spectrometer_code_histogram.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ci]
             lib.spectrometer_code_histogram.restype = ci
             lib.polaris_power_from_histogram.argtypes = [ci, ctypes.POINTER(ctypes.c_uint64),
@@ -122,6 +124,12 @@ def _ptr(x):
     if isinstance(x, np.ndarray):
         return x.ctypes.data
     return int(x.data_ptr())
+
+
+def set_wait_limit(polls: int) -> None:
+    """Test hook: polls per bounded device-side wait for later launches (0: every such wait
+    runs out at once; negative: the default)."""
+    load().polaris_set_wait_limit(int(polls))
 
 
 def power_from_histogram(bits: int, counts) -> tuple[float, float]:
