@@ -291,7 +291,7 @@ struct Plan {
     // on distinct bank pairs)
     static constexpr int row_words(int ipt) { return 2 * (ipt * WARPS * CW * BITS / 32) + 2; }
     static constexpr bool fits(int ipt, int bufs) {
-      return REGIONS1 + 4 * (size_t)bufs * N1 * row_words(ipt) + 16 <= kSmemPerCta2;
+      return REGIONS1 + 4 * (size_t)bufs * N1 * row_words(ipt) + 32 <= kSmemPerCta2;
     }
     static constexpr bool ok(int ipt) {
       return N2 % (ipt * WARPS * CW) == 0 && (ipt * WARPS * CW) % 32 == 0 && fits(ipt, 2);
@@ -303,7 +303,7 @@ struct Plan {
     static constexpr int RS = row_words(IPT);
     static constexpr int NB = fits(IPT, 2) ? 2 : 1;  // 2: the next tile in flight
     static constexpr int WORDS = STAGED ? NB * N1 * RS : 0;
-    static constexpr size_t SMEM = REGIONS1 + 4 * (size_t)WORDS + 16;
+    static constexpr size_t SMEM = REGIONS1 + 4 * (size_t)WORDS + 16 + 16;  // + 2 mbarriers + TMEM slot
   };
 
   // phase 2: a warp owns UPW units; lane = (uw * 2 + e) * Q2 + q2 holds rows q2 + Q2 t

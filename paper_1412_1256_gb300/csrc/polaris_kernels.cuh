@@ -77,6 +77,14 @@ struct BatchArgs {
   unsigned wait_limit;  // iterations of a bounded mbarrier wait before it counts as timed out
 };
 
+// Tensor maps of the packed input for phase 1's TMA staging: m[0][i] views IF i's staged
+// segments [0, n0) and m[1][i] its segments from n0 on, each as words x rows x segments.
+// use = 0: the kernel stages with cp.async instead (layouts a tensor map cannot describe).
+struct InMaps {
+  CUtensorMap m[2][kMaxIF];
+  int use;
+};
+
 __device__ __forceinline__ const uint32_t* seg_ptr(const SegSrc& in, int ifx, int s) {
   return s < in.n0 ? in.src0[ifx] + (long long)s * in.hop_w : in.src1[ifx] + (long long)(s - in.n0) * in.hop_w;
 }
@@ -261,7 +269,7 @@ __device__ __forceinline__ void cta_tmem_end(uint32_t tbase, int warp) {
 // ------------------------------------------------------------------------------------------
 template <int LOGN, int BITS>
 __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
-    k_phase1(BatchArgs a, const __grid_constant__ CUtensorMap slab_map) {
+    k_phase1(BatchArgs a, const __grid_constant__ CUtensorMap slab_map, const __grid_constant__ InMaps in_maps) {
   using PL = Plan<LOGN>;
   constexpr int P = PL::P1, N1 = PL::N1, N2 = PL::N2, Q1 = PL::Q1, CW = PL::CW, PQ = PL::PQ;
   constexpr int LDP = PL::LDP1, LDQ = PL::LDQ1;
@@ -276,8 +284,19 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int q1 = lane / CW, cw = lane % CW;
   float2* region = sm1 + warp * PL::REGION1;
-  uint32_t* stage = reinterpret_cast<uint32_t*>(sm1 + PL::WARPS * PL::REGION1);  // [row][IF pair][WPR]
-  uint32_t* tslot = stage + ST::WORDS;
+  uint32_t* stage = reinterpret_cast<uint32_t*>(sm1 + PL::WARPS * PL::REGION1);  // stage buffers
+  const uint32_t bar0 = smem_addr(stage + ST::WORDS);  // two mbarriers (TMA staging), then the TMEM slot
+  uint32_t* tslot = stage + ST::WORDS + 4;
+  // TMA staging of the input: possible for this plan (two buffers, 16-byte box rows, boxes
+  // of at most 256 rows) and chosen by the host for this launch
+  constexpr bool TIN = STAGED && ST::NB == 2 && (WPR * 4) % 16 == 0 && N1 <= 256;
+  const bool tin = TIN && in_maps.use != 0;
+  if (TIN && tin && tid == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar0 + 8, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    fence_async_shared();
+  }
 
   uint32_t tbase = 0, t_tw = 0;
   if constexpr (Q1 > 1) {
@@ -432,37 +451,102 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
       });
       cp_async_commit();
     };
+    // TMA staging: one thread loads the tile's box of each IF (N1 rows x WPR words) into a
+    // dense [IF][row][word] stage and the CTA waits on that buffer's mbarrier (bounded)
+    auto issue_tma = [&](long long tile, int buf) {
+      const int g = (int)(tile / (N2 / TILE)), b0 = (int)(tile % (N2 / TILE)) * TILE;
+      const int s_local = g / a.n_fpair, f = g - s_local * a.n_fpair;
+      const int sg = a.seg0 + s_local;
+      const int ia = a.fa[f], ib = a.fb[f];
+      const int src = sg < a.in.n0 ? 0 : 1, z = sg < a.in.n0 ? sg : sg - a.in.n0;
+      const uint32_t bar = bar0 + 8u * (uint32_t)buf, dst = stage_a + 4u * (uint32_t)(buf * SB);
+      const uint32_t box = (uint32_t)(N1 * WPR * 4);
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
+                   "r"(ib >= 0 ? 2 * box : box)
+                   : "memory");
+      const int x = (b0 * BITS) / 32;
+      asm volatile(
+          "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+          "[%5];\n" ::"r"(dst),
+          "l"(&in_maps.m[src][ia]), "r"(x), "r"(0), "r"(z), "r"(bar)
+          : "memory");
+      if (ib >= 0)
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+            "[%5];\n" ::"r"(dst + box),
+            "l"(&in_maps.m[src][ib]), "r"(x), "r"(0), "r"(z), "r"(bar)
+            : "memory");
+    };
+    uint32_t par[2] = {0u, 0u};
     long long tile = blockIdx.x;
-    if (tile < n_tiles) issue(tile, 0);
+    if (tile < n_tiles) {
+      if (tin) {
+        if (tid == 0) issue_tma(tile, 0);
+      } else {
+        issue(tile, 0);
+      }
+    }
     for (int buf = 0; tile < n_tiles; tile += gridDim.x, buf = (NB == 2) ? buf ^ 1 : 0) {
-      cp_async_wait_all();
-      __syncthreads();  // this tile's words are staged; every warp is done with the other buffer
+      int timed_out = 0;
+      if (tin) {
+        const uint32_t bar = bar0 + 8u * (uint32_t)buf;
+        if (!mbar_wait_bounded(bar, par[buf], a.wait_limit)) {
+          timed_out = 1;
+          if (lane == 0 && a.err) atomicExch(a.err, 1);
+          mbar_wait_bounded(bar, par[buf], kWaitAfterTimeout);  // the copy in flight lands first
+        }
+        par[buf] ^= 1u;
+      } else {
+        cp_async_wait_all();
+      }
+      // this tile's words are staged; every warp is done with the other buffer
+      if (__syncthreads_or(timed_out)) break;
       const long long next = tile + gridDim.x;
       if constexpr (NB == 2) {
-        if (next < n_tiles) issue(next, buf ^ 1);
+        if (next < n_tiles) {
+          if (tin) {
+            if (tid == 0) {
+              fence_async_shared();  // the CTA's reads of that buffer come before the copy
+              issue_tma(next, buf ^ 1);
+            }
+          } else {
+            issue(next, buf ^ 1);
+          }
+        }
       }
       if (next >= n_tiles) pdl_trigger();  // this CTA's last tile: phase 2 may be scheduled
       const int g = (int)(tile / (N2 / TILE)), b0 = (int)(tile % (N2 / TILE)) * TILE;
       const int f = g % a.n_fpair;
       const bool has_b = a.fb[f] >= 0;
       // IPT column groups per warp per tile: group it of warp w holds columns (it WARPS + w) CW + cw
-      sfor<0, IPT>([&](auto it_) {
-        constexpr int it = decltype(it_)::value;
+      // (a rolled loop: one copy of the decode variants and of the transform in the code)
+#pragma unroll 1
+      for (int it = 0; it < IPT; ++it) {
         const int col = (it * PL::WARPS + warp) * CW + cw;  // column inside the tile
         const long long b = b0 + col;
         const int wd = (col * BITS) >> 5;
         const uint32_t rot = decode_rot<BITS>((uint32_t)((col * BITS) & 31));
-        const uint32_t* sb = stage + buf * SB + 2 * wd;
+        const uint32_t* sb = stage + buf * SB;
         float2 v[P];
-        // decode the lane's 32 rows; the pair's shape and the window are uniform per tile
-        auto decode = [&](auto hb_, auto tp_) {
-          constexpr bool HB = decltype(hb_)::value, TP = decltype(tp_)::value;
+        // decode the lane's rows; the stage layout, the pair's shape and the window are
+        // uniform per tile.  Interleaved layout (cp.async): word w of IF a at 2w, of IF b
+        // at 2w + 1 of row r's RS words.  Dense layout (TMA): [IF][row][WPR].
+        auto decode = [&](auto tl_, auto hb_, auto tp_) {
+          constexpr bool TL = decltype(tl_)::value, HB = decltype(hb_)::value, TP = decltype(tp_)::value;
           sfor<0, P>([&](auto t_) {
             constexpr int t = decltype(t_)::value;
             const int row = q1 + Q1 * t;
-            const uint2 w = *reinterpret_cast<const uint2*>(sb + row * RS);  // IF a, IF b
-            float x = decode_level_rot<BITS>(w.x, rot);
-            float y = HB ? decode_level_rot<BITS>(w.y, rot) : 0.0f;
+            uint32_t wa, wb = 0;
+            if constexpr (TL) {
+              wa = sb[row * WPR + wd];
+              if constexpr (HB) wb = sb[N1 * WPR + row * WPR + wd];
+            } else {
+              const uint2 w = *reinterpret_cast<const uint2*>(sb + row * RS + 2 * wd);  // IF a, IF b
+              wa = w.x;
+              wb = w.y;
+            }
+            float x = decode_level_rot<BITS>(wa, rot);
+            float y = HB ? decode_level_rot<BITS>(wb, rot) : 0.0f;
             if constexpr (TP) {
               const float tv = __ldg(a.taps + row * N2 + b);
               x *= tv;
@@ -473,19 +557,29 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
         };
         using T_ = std::true_type;
         using F_ = std::false_type;
-        if (a.taps) {
-          if (has_b) decode(T_{}, T_{});
-          else decode(F_{}, T_{});
+        auto decode_tl = [&](auto tl) {
+          if (a.taps) {
+            if (has_b) decode(tl, T_{}, T_{});
+            else decode(tl, F_{}, T_{});
+          } else {
+            if (has_b) decode(tl, T_{}, F_{});
+            else decode(tl, F_{}, F_{});
+          }
+        };
+        if constexpr (TIN) {
+          if (tin) decode_tl(T_{});
+          else decode_tl(F_{});
         } else {
-          if (has_b) decode(T_{}, F_{});
-          else decode(F_{}, F_{});
+          decode_tl(F_{});
         }
-        if constexpr (NB == 1 && it == IPT - 1) {
-          __syncthreads();  // every warp has decoded the tile: the single buffer is free
-          if (next < n_tiles) issue(next, 0);
+        if constexpr (NB == 1) {
+          if (it == IPT - 1) {
+            __syncthreads();  // every warp has decoded the tile: the single buffer is free
+            if (next < n_tiles) issue(next, 0);
+          }
         }
         finish(v, true, g, b, b0 + (it * PL::WARPS + warp) * CW);
-      });
+      }
     }
     cp_async_wait_all();
   }
@@ -837,6 +931,31 @@ static cudaError_t encode_slab_map(CUtensorMap* map, float2* slab, long long row
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Tensor map over one IF's packed input: 32-bit words x rows (row_bytes apart) x segments
+// (seg_bytes apart); box = one tile's words of all rows of one segment.  Fails (and phase 1
+// then stages with cp.async) for an address that is not 16-byte aligned.
+static cudaError_t encode_input_map(CUtensorMap* map, const uint32_t* base, int words_per_row, int rows,
+                                    long long segs, long long row_bytes, long long seg_bytes, int box_words) {
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0) return cudaErrorMisalignedAddress;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)words_per_row, (cuuint64_t)rows, (cuuint64_t)segs};
+  const cuuint64_t strides[2] = {(cuuint64_t)row_bytes, (cuuint64_t)seg_bytes};
+  const cuuint32_t box[3] = {(cuuint32_t)box_words, (cuuint32_t)rows, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<uint32_t*>(base), dims, strides, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int LOGN, int BITS>
 static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st, bool pdl) {
   using PL = Plan<LOGN>;
@@ -858,6 +977,28 @@ static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st, bool pdl) 
     const cudaError_t e = encode_slab_map(&map, a.scratch, (long long)a.nseg * a.n_fpair * PL::N1, PL::N2, PL::CW, PL::N1);
     if (e != cudaSuccess) return e;
   }
+  // input maps for TMA staging (else the kernel stages with cp.async)
+  static thread_local InMaps in_maps;  // 2 KB: kept off the stack; filled, then copied by the launch
+  in_maps.use = 0;
+  constexpr int WPR_T = ST::STAGED ? ST::WPR : 1;
+  if constexpr (ST::STAGED && ST::NB == 2 && (WPR_T * 4) % 16 == 0 && PL::N1 <= 256) {
+    const long long row_bytes = (long long)PL::N2 * BITS / 8, seg_bytes = a.in.hop_w * 4;
+    bool ok = row_bytes % 16 == 0 && seg_bytes % 16 == 0;
+    const int seg_end = a.seg0 + a.nseg;  // segments [0, seg_end) of the feed are addressable
+    for (int f = 0; f < a.n_fpair && ok; ++f)
+      for (int k = 0; k < 2 && ok; ++k) {
+        const int ifx = k == 0 ? a.fa[f] : a.fb[f];
+        if (ifx < 0) continue;
+        for (int src = 0; src < 2 && ok; ++src) {
+          const long long nseg_src = src == 0 ? a.in.n0 : (long long)seg_end - a.in.n0;
+          if (nseg_src <= 0) continue;
+          const uint32_t* base = src == 0 ? a.in.src0[ifx] : a.in.src1[ifx];
+          ok = encode_input_map(&in_maps.m[src][ifx], base, PL::N2 * BITS / 32, PL::N1, nseg_src, row_bytes,
+                                seg_bytes, WPR_T) == cudaSuccess;
+        }
+      }
+    in_maps.use = ok ? 1 : 0;
+  }
   const long long cols = (long long)a.nseg * a.n_fpair * PL::N2;
   const long long ctas = ST::STAGED ? cols / ST::TILE  // one tile per CTA pass
                                      : ((cols + PL::CW - 1) / PL::CW + PL::WARPS - 1) / PL::WARPS;
@@ -872,7 +1013,7 @@ static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st, bool pdl) 
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, k_phase1<LOGN, BITS>, a, map);
+  return cudaLaunchKernelEx(&cfg, k_phase1<LOGN, BITS>, a, map, in_maps);
 }
 
 // phase 1 of one batch
