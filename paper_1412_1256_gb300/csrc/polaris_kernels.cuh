@@ -477,16 +477,26 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
             "l"(&in_maps.m[src][ib]), "r"(x), "r"(0), "r"(z), "r"(bar)
             : "memory");
     };
+    // Work units: whole tiles for the complete rounds over the grid, then, for the last,
+    // partial round, half tiles (one column group per warp; the whole tile is staged), so
+    // that the last round spreads over twice as many CTAs.
+    const long long G = gridDim.x;
+    long long F = n_tiles;  // units [0, F) are whole tiles, [F, ...) halves of the rest
+    if (IPT == 2 && n_tiles % G != 0) F = (n_tiles / G) * G;
+    const long long n_units = F + (n_tiles - F) * (IPT == 2 ? 2 : 1);
+    auto unit_tile = [&](long long u) { return u < F ? u : F + (u - F) / 2; };
     uint32_t par[2] = {0u, 0u};
-    long long tile = blockIdx.x;
-    if (tile < n_tiles) {
+    long long unit = blockIdx.x;
+    if (unit < n_units) {
       if (tin) {
-        if (tid == 0) issue_tma(tile, 0);
+        if (tid == 0) issue_tma(unit_tile(unit), 0);
       } else {
-        issue(tile, 0);
+        issue(unit_tile(unit), 0);
       }
     }
-    for (int buf = 0; tile < n_tiles; tile += gridDim.x, buf = (NB == 2) ? buf ^ 1 : 0) {
+    for (int buf = 0; unit < n_units; unit += G, buf = (NB == 2) ? buf ^ 1 : 0) {
+      const long long tile = unit_tile(unit);
+      const int it_begin = unit < F ? 0 : (int)((unit - F) & 1), it_end = unit < F ? IPT : it_begin + 1;
       int timed_out = 0;
       if (tin) {
         const uint32_t bar = bar0 + 8u * (uint32_t)buf;
@@ -501,27 +511,27 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
       }
       // this tile's words are staged; every warp is done with the other buffer
       if (__syncthreads_or(timed_out)) break;
-      const long long next = tile + gridDim.x;
+      const long long next = unit + G;
       if constexpr (NB == 2) {
-        if (next < n_tiles) {
+        if (next < n_units) {
           if (tin) {
             if (tid == 0) {
               fence_async_shared();  // the CTA's reads of that buffer come before the copy
-              issue_tma(next, buf ^ 1);
+              issue_tma(unit_tile(next), buf ^ 1);
             }
           } else {
-            issue(next, buf ^ 1);
+            issue(unit_tile(next), buf ^ 1);
           }
         }
       }
-      if (next >= n_tiles) pdl_trigger();  // this CTA's last tile: phase 2 may be scheduled
+      if (next >= n_units) pdl_trigger();  // this CTA's last unit: phase 2 may be scheduled
       const int g = (int)(tile / (N2 / TILE)), b0 = (int)(tile % (N2 / TILE)) * TILE;
       const int f = g % a.n_fpair;
       const bool has_b = a.fb[f] >= 0;
       // IPT column groups per warp per tile: group it of warp w holds columns (it WARPS + w) CW + cw
       // (a rolled loop: one copy of the decode variants and of the transform in the code)
 #pragma unroll 1
-      for (int it = 0; it < IPT; ++it) {
+      for (int it = it_begin; it < it_end; ++it) {
         const int col = (it * PL::WARPS + warp) * CW + cw;  // column inside the tile
         const long long b = b0 + col;
         const int wd = (col * BITS) >> 5;
@@ -573,9 +583,9 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
           decode_tl(F_{});
         }
         if constexpr (NB == 1) {
-          if (it == IPT - 1) {
+          if (it == it_end - 1) {
             __syncthreads();  // every warp has decoded the tile: the single buffer is free
-            if (next < n_tiles) issue(next, 0);
+            if (next < n_units) issue(unit_tile(next), 0);
           }
         }
         finish(v, true, g, b, b0 + (it * PL::WARPS + warp) * CW);
@@ -635,7 +645,9 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
 
   for (int k = tid; k < N2; k += PL::THREADS) tw2[k + (k >> 5)] = tw_small<N2>(k);
   const uint32_t tbase = cta_tmem_begin<PL::TCOLS2>(tslot, warp);  // (its barrier also publishes tw2)
-  pdl_wait();  // the slab written by phase 1 (and the accumulators cleared by the readout) are visible
+  // (pdl_wait -- the slab written by phase 1 and the accumulators cleared by the readout are
+  // visible -- comes after the first item's tensor-memory set-up, which reads neither)
+  bool waited = false;
   const uint32_t t_acc = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * (PL::TCOLS2 / 2));
   const uint32_t t_tw = t_acc + TACC;
 
@@ -674,6 +686,10 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
       tmem_st16(t_tw + 16 * cc, w16);
     });
     tmem_wait_st();
+    if (!waited) {
+      pdl_wait();
+      waited = true;
+    }
     float extra[4] = {0.f, 0.f, 0.f, 0.f};
     bool worked = false;
     const int r_end = min(R, (rg + 1) * range_len);
@@ -1000,7 +1016,8 @@ static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st, bool pdl) 
     in_maps.use = ok ? 1 : 0;
   }
   const long long cols = (long long)a.nseg * a.n_fpair * PL::N2;
-  const long long ctas = ST::STAGED ? cols / ST::TILE  // one tile per CTA pass
+  // staged: one unit (a tile, or half of one in the last round) per CTA pass
+  const long long ctas = ST::STAGED ? (cols / ST::TILE) * ST::IPT
                                      : ((cols + PL::CW - 1) / PL::CW + PL::WARPS - 1) / PL::WARPS;
   const long long cap = (long long)per_sm * a.num_sms;
   cudaLaunchConfig_t cfg = {};
