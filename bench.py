@@ -269,10 +269,26 @@ def batch_graph_variant(torch, polaris, dev, local_rank, world, n_streams=64, se
         items.append((sp, dev_in, n, outs))
         total += 2 * n
 
+    # the handles spread over side streams (largest first, round robin) so that small
+    # transforms run side by side; forked from and joined back into the issuing stream
+    side = [torch.cuda.Stream(dev) for _ in range(8)]
+    order = sorted(range(len(items)), key=lambda i: -items[i][2])
+
     def issue_all(cs):
-        for sp, dev_in, n, outs in items:
-            sp.feed(dev_in, n, on_device=True, stream=cs)
-            sp.integrate_device(*outs, stream=cs)
+        fork = torch.cuda.Event()
+        fork.record(cs)
+        joins = []
+        for k, ss in enumerate(side):
+            ss.wait_event(fork)
+            for i in order[k::len(side)]:
+                sp, dev_in, n, outs = items[i]
+                sp.feed(dev_in, n, on_device=True, stream=ss)
+                sp.integrate_device(*outs, stream=ss)
+            ev = torch.cuda.Event()
+            ev.record(ss)
+            joins.append(ev)
+        for ev in joins:
+            cs.wait_event(ev)
 
     with torch.cuda.stream(stream):
         issue_all(stream)  # per-kernel set-up outside the capture
