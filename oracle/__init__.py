@@ -18,4 +18,6 @@ from .oracle import (  # noqa: F401
     default_pairs,
     code_histogram,
     power,
+    leak_forward,
+    leak_grad,
 )

@@ -61,12 +61,17 @@ def _load():
                                                   ctypes.POINTER(ctypes.c_void_p), ctypes.c_int64,
                                                   ctypes.POINTER(ctypes.c_uint64)]
             lib.oracle_power.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), _D, _D]
+            lib.oracle_leak_forward.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_void_p),
+                                                ctypes.c_int64, _D, _D, _D, _D, _D, _D]
+            lib.oracle_leak_grad.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_void_p),
+                                             ctypes.c_int64, _D, _D, _D, _D, _D, _D, _D]
             lib.oracle_accumulate.argtypes = [
                 ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _F, ctypes.c_int, _I32,
                 ctypes.POINTER(_U32), ctypes.c_int64, _D, _D, _I64,
             ]
             for f in ("oracle_decode", "oracle_window", "oracle_dft", "oracle_fft", "oracle_stokes", "oracle_accumulate",
-                      "oracle_spectra_levels", "oracle_code_histogram", "oracle_power"):
+                      "oracle_spectra_levels", "oracle_code_histogram", "oracle_power", "oracle_leak_forward",
+                      "oracle_leak_grad"):
                 getattr(lib, f).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -219,3 +224,32 @@ def power(bits: int, counts) -> tuple[float, float]:
     _check(_load().oracle_power(bits, c.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _p(m2, _D), _p(sg, _D)),
            "power")
     return float(m2[0]), float(sg[0])
+
+
+def _leak_args(packed, window, gains, leak, target):
+    words = [np.ascontiguousarray(p, dtype=np.uint32) for p in packed]
+    arr = (ctypes.c_void_p * 2)(*[w.ctypes.data for w in words])
+    f = [np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1)) if x is not None else None
+         for x in (window, gains, leak, target)]
+    return words, arr, f
+
+
+def leak_forward(packed, bits: int, n_fft: int, n_samples: int, window, gains, leak, target=None):
+    """(stokes [4, nbin], loss or None) of the leakage model (circular feeds, two IFs)."""
+    words, arr, (w, g, d, t) = _leak_args(packed, window, gains, leak, target)
+    nbin = n_fft // 2 + 1
+    st = np.zeros(4 * nbin)
+    loss = np.zeros(1)
+    _check(_load().oracle_leak_forward(bits, n_fft, arr, n_samples, _p(w, _D), _p(g, _D), _p(d, _D),
+                                       None if t is None else _p(t, _D), _p(st, _D), _p(loss, _D)), "leak_forward")
+    return st.reshape(4, nbin), (float(loss[0]) if t is not None else None)
+
+
+def leak_grad(packed, bits: int, n_fft: int, n_samples: int, window, gains, leak, target):
+    """Gradients of the loss: (grad_window [N], grad_gains [4], grad_leak [2, nbin, 2])."""
+    words, arr, (w, g, d, t) = _leak_args(packed, window, gains, leak, target)
+    nbin = n_fft // 2 + 1
+    gw, gg, gd = np.zeros(n_fft), np.zeros(4), np.zeros(4 * nbin)
+    _check(_load().oracle_leak_grad(bits, n_fft, arr, n_samples, _p(w, _D), _p(g, _D), _p(d, _D), _p(t, _D),
+                                    _p(gw, _D), _p(gg, _D), _p(gd, _D)), "leak_grad")
+    return gw, gg, gd.reshape(2, nbin, 2)

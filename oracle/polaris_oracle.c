@@ -318,3 +318,157 @@ int oracle_power(int bits, const uint64_t* counts, double* moment2, double* sigm
   }
   return OR_OK;
 }
+
+/* ---- Differentiable leakage calibration (our model: the paper treats gains as offline
+ * calibration, Sec. 2.1, and is silent on polarisation leakage) ----
+ * Two IFs R and L (circular feeds), segments s of n_fft samples at hop n_fft, window w:
+ *   X_s[k] = sum_n w[n] x_s[n] e^{-2 pi i n k / N},  Y_s[k] likewise, k = 0..N/2
+ *   leakage:  Xt = gR (X + DR[k] Y),   Yt = gL (Y + DL[k] X)
+ *   RR = sum_s |Xt|^2,  LL = sum_s |Yt|^2,  RL = sum_s Xt conj(Yt)
+ *   I = (RR + LL)/2,  V = (RR - LL)/2,  Q = Re RL,  U = Im RL      (circular feeds, psi = 0)
+ *   loss = sum_k sum_{S = I, Q, U, V} (S[k] - T_S[k])^2
+ * Layouts: gains = (gR re, gR im, gL re, gL im); leak = DR then DL, each nbin (re, im);
+ * target and stokes = I, Q, U, V, each nbin.  Plain loops over segments and bins; each
+ * segment's spectra come from oracle_fft of the windowed levels (one IF at a time). */
+typedef struct { double re, im; } ocplx;
+static ocplx oc(double re, double im) { ocplx z = {re, im}; return z; }
+static ocplx oc_add(ocplx a, ocplx b) { return oc(a.re + b.re, a.im + b.im); }
+static ocplx oc_mul(ocplx a, ocplx b) { return oc(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+static ocplx oc_conj(ocplx a) { return oc(a.re, -a.im); }
+static ocplx oc_scale(ocplx a, double s) { return oc(a.re * s, a.im * s); }
+
+/* spectra X, Y (nbin each) of segment s */
+static int leak_segment_spectra(int bits, int64_t N, const uint32_t* const* packed, int64_t s, const double* w,
+                                double* lev, double* re, double* im, ocplx* X, ocplx* Y) {
+  const int64_t nbin = N / 2 + 1;
+  for (int ab = 0; ab < 2; ++ab) {
+    /* levels of samples [s N, s N + N): decode from the segment's first word */
+    const int64_t per_word = 32 / bits;
+    int rc = oracle_decode(bits, packed[ab] + (s * N) / per_word, N, lev);
+    if (rc) return rc;
+    for (int64_t n = 0; n < N; ++n) { re[n] = w[n] * lev[n]; im[n] = 0.0; }
+    rc = oracle_fft(N, re, im);
+    if (rc) return rc;
+    ocplx* out = ab == 0 ? X : Y;
+    for (int64_t k = 0; k < nbin; ++k) out[k] = oc(re[k], im[k]);
+  }
+  return OR_OK;
+}
+
+int oracle_leak_forward(int bits, int64_t N, const uint32_t* const* packed, int64_t n_samples, const double* w,
+                        const double* gains, const double* leak, const double* target, double* stokes, double* loss) {
+  if (!(bits == 1 || bits == 2 || bits == 4 || bits == 8) || N < 2 || (N & (N - 1)) || N % (32 / bits) || !packed ||
+      !w || !gains || !leak || n_samples < N || n_samples % N)
+    return OR_EINVAL;
+  const int64_t nbin = N / 2 + 1, nseg = n_samples / N;
+  double* lev = (double*)malloc(sizeof(double) * (size_t)N);
+  double* re = (double*)malloc(sizeof(double) * (size_t)N);
+  double* im = (double*)malloc(sizeof(double) * (size_t)N);
+  ocplx* X = (ocplx*)malloc(sizeof(ocplx) * (size_t)nbin);
+  ocplx* Y = (ocplx*)malloc(sizeof(ocplx) * (size_t)nbin);
+  double* acc = (double*)calloc((size_t)(4 * nbin), sizeof(double)); /* RR, LL, RL re, RL im */
+  int rc = (lev && re && im && X && Y && acc) ? OR_OK : OR_ENOMEM;
+  const ocplx gR = oc(gains[0], gains[1]), gL = oc(gains[2], gains[3]);
+  for (int64_t s = 0; s < nseg && rc == OR_OK; ++s) {
+    rc = leak_segment_spectra(bits, N, packed, s, w, lev, re, im, X, Y);
+    for (int64_t k = 0; k < nbin && rc == OR_OK; ++k) {
+      const ocplx DR = oc(leak[2 * k], leak[2 * k + 1]), DL = oc(leak[2 * (nbin + k)], leak[2 * (nbin + k) + 1]);
+      const ocplx Xt = oc_mul(gR, oc_add(X[k], oc_mul(DR, Y[k])));
+      const ocplx Yt = oc_mul(gL, oc_add(Y[k], oc_mul(DL, X[k])));
+      const ocplx rl = oc_mul(Xt, oc_conj(Yt));
+      acc[k] += Xt.re * Xt.re + Xt.im * Xt.im;
+      acc[nbin + k] += Yt.re * Yt.re + Yt.im * Yt.im;
+      acc[2 * nbin + k] += rl.re;
+      acc[3 * nbin + k] += rl.im;
+    }
+  }
+  double L = 0.0;
+  for (int64_t k = 0; k < nbin && rc == OR_OK; ++k) {
+    const double S[4] = {0.5 * (acc[k] + acc[nbin + k]), acc[2 * nbin + k], acc[3 * nbin + k],
+                         0.5 * (acc[k] - acc[nbin + k])};
+    for (int q = 0; q < 4; ++q) {
+      if (stokes) stokes[q * nbin + k] = S[q];
+      if (target) {
+        const double d = S[q] - target[q * nbin + k];
+        L += d * d;
+      }
+    }
+  }
+  if (loss && rc == OR_OK) *loss = L;
+  free(lev); free(re); free(im); free(X); free(Y); free(acc);
+  return rc;
+}
+
+/* Gradient of that loss.  With r_S = 2 (S - T_S) per bin, a = (r_I + r_V)/2, b = (r_I - r_V)/2
+ * and c = r_Q + i r_U, each segment contributes, per bin,
+ *   G_Xt = 2a Xt + c Yt,  G_Yt = 2b Yt + conj(c) Xt          (G = 2 dL/d conj(z): dL = Re sum conj(G) dz)
+ *   G_X = conj(gR) G_Xt + conj(gL DL) G_Yt,   G_Y = conj(gR DR) G_Xt + conj(gL) G_Yt
+ *   grad gR += conj(X + DR Y) G_Xt,   grad gL += conj(Y + DL X) G_Yt
+ *   grad DR[k] += conj(gR Y) G_Xt,    grad DL[k] += conj(gL X) G_Yt
+ *   grad w[n] += x[n] Re A_X[n] + y[n] Re A_Y[n],  A = DFT of conj(G) over k = 0..N/2 (zero above)
+ * Complex gradients are returned as (d loss / d re, d loss / d im). */
+int oracle_leak_grad(int bits, int64_t N, const uint32_t* const* packed, int64_t n_samples, const double* w,
+                     const double* gains, const double* leak, const double* target, double* grad_w, double* grad_gains,
+                     double* grad_leak) {
+  if (!target || !grad_w || !grad_gains || !grad_leak) return OR_EINVAL;
+  const int64_t nbin = N / 2 + 1, nseg = n_samples / N;
+  double* S = (double*)malloc(sizeof(double) * (size_t)(4 * nbin));
+  if (!S) return OR_ENOMEM;
+  int rc = oracle_leak_forward(bits, N, packed, n_samples, w, gains, leak, target, S, NULL);
+  if (rc) { free(S); return rc; }
+  double* lev = (double*)malloc(sizeof(double) * (size_t)N * 2);
+  double* re = (double*)malloc(sizeof(double) * (size_t)N);
+  double* im = (double*)malloc(sizeof(double) * (size_t)N);
+  ocplx* X = (ocplx*)malloc(sizeof(ocplx) * (size_t)nbin);
+  ocplx* Y = (ocplx*)malloc(sizeof(ocplx) * (size_t)nbin);
+  ocplx* GX = (ocplx*)malloc(sizeof(ocplx) * (size_t)nbin);
+  ocplx* GY = (ocplx*)malloc(sizeof(ocplx) * (size_t)nbin);
+  rc = (lev && re && im && X && Y && GX && GY) ? OR_OK : OR_ENOMEM;
+  for (int64_t n = 0; n < N; ++n) grad_w[n] = 0.0;
+  for (int q = 0; q < 4; ++q) grad_gains[q] = 0.0;
+  for (int64_t j = 0; j < 4 * nbin; ++j) grad_leak[j] = 0.0;
+  const ocplx gR = oc(gains[0], gains[1]), gL = oc(gains[2], gains[3]);
+  ocplx ggR = oc(0, 0), ggL = oc(0, 0);
+  for (int64_t s = 0; s < nseg && rc == OR_OK; ++s) {
+    rc = leak_segment_spectra(bits, N, packed, s, w, lev, re, im, X, Y);
+    for (int64_t k = 0; k < nbin && rc == OR_OK; ++k) {
+      const double rI = 2.0 * (S[k] - target[k]), rQ = 2.0 * (S[nbin + k] - target[nbin + k]);
+      const double rU = 2.0 * (S[2 * nbin + k] - target[2 * nbin + k]), rV = 2.0 * (S[3 * nbin + k] - target[3 * nbin + k]);
+      const double a = 0.5 * (rI + rV), b = 0.5 * (rI - rV);
+      const ocplx c = oc(rQ, rU);
+      const ocplx DR = oc(leak[2 * k], leak[2 * k + 1]), DL = oc(leak[2 * (nbin + k)], leak[2 * (nbin + k) + 1]);
+      const ocplx uR = oc_add(X[k], oc_mul(DR, Y[k])), uL = oc_add(Y[k], oc_mul(DL, X[k]));
+      const ocplx Xt = oc_mul(gR, uR), Yt = oc_mul(gL, uL);
+      const ocplx GXt = oc_add(oc_scale(Xt, 2.0 * a), oc_mul(c, Yt));
+      const ocplx GYt = oc_add(oc_scale(Yt, 2.0 * b), oc_mul(oc_conj(c), Xt));
+      GX[k] = oc_add(oc_mul(oc_conj(gR), GXt), oc_mul(oc_conj(oc_mul(gL, DL)), GYt));
+      GY[k] = oc_add(oc_mul(oc_conj(oc_mul(gR, DR)), GXt), oc_mul(oc_conj(gL), GYt));
+      ggR = oc_add(ggR, oc_mul(oc_conj(uR), GXt));
+      ggL = oc_add(ggL, oc_mul(oc_conj(uL), GYt));
+      const ocplx gDR = oc_mul(oc_conj(oc_mul(gR, Y[k])), GXt), gDL = oc_mul(oc_conj(oc_mul(gL, X[k])), GYt);
+      grad_leak[2 * k] += gDR.re;
+      grad_leak[2 * k + 1] += gDR.im;
+      grad_leak[2 * (nbin + k)] += gDL.re;
+      grad_leak[2 * (nbin + k) + 1] += gDL.im;
+    }
+    /* window: levels of this segment again (x, y), then the DFT of conj(G) */
+    const int64_t per_word = 32 / bits;
+    if (rc == OR_OK) rc = oracle_decode(bits, packed[0] + (s * N) / per_word, N, lev);
+    if (rc == OR_OK) rc = oracle_decode(bits, packed[1] + (s * N) / per_word, N, lev + N);
+    for (int ab = 0; ab < 2 && rc == OR_OK; ++ab) {
+      const ocplx* G = ab == 0 ? GX : GY;
+      for (int64_t k = 0; k < N; ++k) {
+        re[k] = k < nbin ? G[k].re : 0.0;
+        im[k] = k < nbin ? -G[k].im : 0.0;
+      }
+      rc = oracle_fft(N, re, im);
+      for (int64_t n = 0; n < N && rc == OR_OK; ++n) grad_w[n] += lev[ab * N + n] * re[n];
+    }
+  }
+  grad_gains[0] = ggR.re;
+  grad_gains[1] = ggR.im;
+  grad_gains[2] = ggL.re;
+  grad_gains[3] = ggL.im;
+  free(S); free(lev); free(re); free(im); free(X); free(Y); free(GX); free(GY);
+  return rc;
+}
