@@ -222,6 +222,40 @@ int spectrometer_code_histogram(polaris_spec* s, uint64_t* counts, int reset);
  * counts or an empty histogram. */
 int polaris_power_from_histogram(int bits, const uint64_t* counts, double* moment2, double* sigma_over_threshold);
 
+/* ---- Differentiable leakage calibration ----
+ * A model of our own (the paper calibrates the gains offline, Sec. 2.1, and does not
+ * model polarisation leakage) with a hand-written adjoint, for fitting a window, the two
+ * feeds' complex gains and per-channel leakage to target Stokes spectra.  Two IFs R and L
+ * (circular feeds), segments of n_fft samples at hop n_fft, window w (n_fft taps):
+ *   X_s[k] = sum_n w[n] x_s[n] e^{-2 pi i n k / N},  Y_s[k] likewise, k = 0..N/2
+ *   Xt = gR (X + DR[k] Y),   Yt = gL (Y + DL[k] X)
+ *   RR = sum_s |Xt|^2, LL = sum_s |Yt|^2, RL = sum_s Xt conj(Yt)
+ *   I = (RR + LL)/2, Q = Re RL, U = Im RL, V = (RR - LL)/2     (circular feeds, psi = 0)
+ *   loss = sum_k sum_{S = I, Q, U, V} (S[k] - T_S[k])^2
+ * polaris_adj_create: n_fft a power of two in [32, 16384], bits 1/2/4/8; allocates a
+ * handle with its twiddles and accumulators on `device`.
+ * polaris_adj_run: all pointers are DEVICE pointers, fp32 unless stated, queued on
+ * cuda_stream (NULL = legacy stream), nothing synchronises the host:
+ *   packed[2]    the two IFs' packed codes (layout as spectrometer_feed), n_samples each,
+ *                a positive multiple of n_fft
+ *   window       n_fft taps;  gains  (gR re, gR im, gL re, gL im)
+ *   leak         DR then DL, each n_fft/2+1 (re, im) pairs
+ *   target       I, Q, U, V, each n_fft/2+1 (NULL: no loss, no gradients)
+ *   stokes       out: I, Q, U, V of the model, each n_fft/2+1 (NULL skips)
+ *   loss         out: one fp64 value (NULL skips)
+ *   grad_window, grad_gains, grad_leak   out: d loss / d (each real parameter), in the
+ *                layouts of the inputs; all three or none.  The adjoint transforms every
+ *                segment again instead of storing the spectra.
+ * Errors: POLARIS_EINVAL for bad arguments, POLARIS_ECUDA for a CUDA error (text from
+ * polaris_adj_last_error; NULL handle: the last failed create in this thread). */
+typedef struct polaris_adj polaris_adj;
+int polaris_adj_create(int64_t n_fft, int bits, int device, polaris_adj** out);
+int polaris_adj_run(polaris_adj* h, const void* const* packed, int64_t n_samples, const float* window,
+                    const float* gains, const float* leak, const float* target, float* stokes, double* loss,
+                    float* grad_window, float* grad_gains, float* grad_leak, void* cuda_stream);
+void polaris_adj_destroy(polaris_adj* h);
+const char* polaris_adj_last_error(const polaris_adj* h);
+
 /* Bounded device-side waits.  Phase 2 (N >= 2^17) prefetches its next columns with
  * asynchronous bulk copies and waits for them on a shared-memory barrier; every such wait
  * polls at most a fixed number of times.  If one runs out, the kernel records the fact in

@@ -29,6 +29,7 @@ EXPORTS = (
     "spectrometer_last_error", "polaris_set_alloc_limit", "spectrometer_kernel_launches",
     "spectrometer_set_profiling", "spectrometer_kernel_times", "spectrometer_run_noalloc",
     "spectrometer_code_histogram", "polaris_power_from_histogram", "polaris_set_wait_limit",
+    "polaris_adj_create", "polaris_adj_run", "polaris_adj_destroy", "polaris_adj_last_error",
 )
 
 
@@ -96,6 +97,14 @@ def load(path: str = LIB_PATH):
             lib.spectrometer_run_noalloc.restype = ci
             lib.polaris_set_alloc_limit.argtypes = [i64]
             lib.polaris_set_alloc_limit.restype = None
+            lib.polaris_adj_create.argtypes = [i64, ci, ci, ctypes.POINTER(vp)]
+            lib.polaris_adj_create.restype = ci
+            lib.polaris_adj_run.argtypes = [vp, ctypes.POINTER(vp), i64] + [vp] * 10
+            lib.polaris_adj_run.restype = ci
+            lib.polaris_adj_destroy.argtypes = [vp]
+            lib.polaris_adj_destroy.restype = None
+            lib.polaris_adj_last_error.argtypes = [vp]
+            lib.polaris_adj_last_error.restype = ctypes.c_char_p
             lib.polaris_set_wait_limit.argtypes = [i64]
             lib.polaris_set_wait_limit.restype = None
             lib.spectrometer_code_histogram.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ci]
@@ -334,3 +343,84 @@ def run_noalloc(packed, n_samples: int, bits: int, n_fft: int, autos, cross, sto
     if rc != OK:
         raise PolarisError(rc, lib.spectrometer_last_error(None).decode())
     return int(nseg.value)
+
+
+class Adjoint:
+    """Differentiable leakage calibration (polaris_adj_*): forward model, loss and
+    gradients for two circular-feed IFs.  Tensors are CUDA tensors (float32 unless stated)."""
+
+    def __init__(self, n_fft: int, bits: int, device: int = 0):
+        h = ctypes.c_void_p()
+        rc = load().polaris_adj_create(int(n_fft), int(bits), int(device), ctypes.byref(h))
+        if rc != OK:
+            raise PolarisError(rc, load().polaris_adj_last_error(None).decode())
+        self._h, self.n_fft, self.bits, self.device = h, n_fft, bits, device
+        self.n_bins = n_fft // 2 + 1
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().polaris_adj_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def run(self, packed, n_samples: int, window, gains, leak, target=None, grads: bool = False, stream=None):
+        """dict(stokes [4, nb], loss (float64, 1 element) and, with grads=True, grad_window [N],
+        grad_gains [4], grad_leak [2, nb, 2]).  packed: two CUDA tensors of packed words."""
+        import torch
+
+        dev = window.device
+        nb = self.n_bins
+        out = {"stokes": torch.empty((4, nb), dtype=torch.float32, device=dev)}
+        if target is not None:
+            out["loss"] = torch.empty((1,), dtype=torch.float64, device=dev)
+        if grads:
+            out["grad_window"] = torch.empty((self.n_fft,), dtype=torch.float32, device=dev)
+            out["grad_gains"] = torch.empty((4,), dtype=torch.float32, device=dev)
+            out["grad_leak"] = torch.empty((2, nb, 2), dtype=torch.float32, device=dev)
+        arr = (ctypes.c_void_p * 2)(*[_ptr(p) for p in packed])
+        ins = [t.contiguous() for t in (window, gains, leak)]
+        tgt = None if target is None else target.contiguous()
+        rc = load().polaris_adj_run(self._h, arr, int(n_samples), _ptr(ins[0]), _ptr(ins[1]), _ptr(ins[2]),
+                                    None if tgt is None else _ptr(tgt), _ptr(out["stokes"]),
+                                    _ptr(out["loss"]) if "loss" in out else None,
+                                    _ptr(out["grad_window"]) if grads else None,
+                                    _ptr(out["grad_gains"]) if grads else None,
+                                    _ptr(out["grad_leak"]) if grads else None, _stream_ptr(stream))
+        if rc != OK:
+            raise PolarisError(rc, load().polaris_adj_last_error(self._h).decode())
+        return out
+
+
+def leakage_loss(adj: "Adjoint", packed, n_samples: int, window, gains, leak, target):
+    """The calibration loss as a differentiable function of window, gains and leak
+    (torch.autograd), its gradient from the library's adjoint."""
+    import torch
+
+    class _LeakageLoss(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, w, g, d):
+            need = any(ctx.needs_input_grad)
+            r = adj.run(packed, n_samples, w.detach(), g.detach(), d.detach(), target, grads=need,
+                        stream=torch.cuda.current_stream(w.device))
+            if need:
+                ctx.save_for_backward(r["grad_window"], r["grad_gains"], r["grad_leak"])
+            return r["loss"][0]
+
+        @staticmethod
+        def backward(ctx, gout):
+            gw, gg, gd = ctx.saved_tensors
+            s = gout.to(torch.float32)
+            return s * gw, s * gg, s * gd
+
+    return _LeakageLoss.apply(window, gains, leak)
