@@ -8,21 +8,40 @@
 //   RR = sum_s |Xt|^2, LL = sum_s |Yt|^2, RL = sum_s Xt conj(Yt)
 //   I = (RR + LL)/2, V = (RR - LL)/2, Q = Re RL, U = Im RL
 //   loss = sum_k sum_S (S[k] - T_S[k])^2
-// Adjoint: with r_S = 2 (S - T_S), a = (r_I + r_V)/2, b = (r_I - r_V)/2, c = r_Q + i r_U,
-//   G_Xt = 2a Xt + c Yt,  G_Yt = 2b Yt + conj(c) Xt          (G = 2 dL/d conj(z))
-//   G_X = conj(gR) G_Xt + conj(gL DL) G_Yt,  G_Y = conj(gR DR) G_Xt + conj(gL) G_Yt
-//   grad gR = sum conj(X + DR Y) G_Xt,  grad gL = sum conj(Y + DL X) G_Yt
-//   grad DR[k] = sum_s conj(gR Y) G_Xt,  grad DL[k] = sum_s conj(gL X) G_Yt
-//   grad w[n] = sum_s x[n] Re(sum_k G_X[k] e^{+2 pi i n k/N}) + y[n] Re(sum_k G_Y[k] e^{+...})
-// The last sums are real inverse transforms of the one-sided G: the Hermitian extensions of
-// G_X and G_Y go through one complex inverse FFT as H_X + i H_Y.  Segments are transformed
-// again in the adjoint pass, not stored.
 //
-// Kernels: one CTA per segment holds the segment's N complex points in shared memory
-// (N <= 16384: 128 KB) and runs an in-place radix-2 transform; the pair x + i y is
-// transformed once.
+// The mixing is linear per bin, so RR, LL and RL are quadratic forms of the plain sums
+//   A = sum_s |X|^2, B = sum_s |Y|^2, C = sum_s X conj(Y):
+//   P_R = sum|X + DR Y|^2 = A + |DR|^2 B + 2 Re(conj(DR) C)
+//   P_L = sum|Y + DL X|^2 = B + |DL|^2 A + 2 Re(DL C)
+//   Qm  = sum (X + DR Y) conj(Y + DL X) = C + conj(DL) A + DR B + DR conj(DL) conj(C)
+//   RR = |gR|^2 P_R, LL = |gL|^2 P_L, RL = gR conj(gL) Qm.
+// Gradients use G = dL/d re + i dL/d im for every complex parameter.  With r_S = 2 (S - T_S),
+// a = (r_I + r_V)/2, b = (r_I - r_V)/2, c = r_Q + i r_U:
+//   G_gR = sum_k 2a P_R gR + c gL conj(Qm)          G_gL = sum_k 2b P_L gL + conj(c) gR Qm
+//   G_DR[k] = 2a |gR|^2 (B DR + C) + c conj(gR) gL (B + DL C)
+//   G_DL[k] = 2b |gL|^2 (A DL + conj(C)) + conj(c) gR conj(gL) (A + DR conj(C))
+// so neither needs the segments again.  The window does: per segment the spectral
+// gradients are G_X = m11 X + m12 Y, G_Y = m21 X + m22 Y with a per-bin 2 x 2 matrix (from
+// G_Xt = 2a Xt + c Yt, G_Yt = 2b Yt + conj(c) Xt pulled back through the mixing), and
+//   dL/dw[n] = sum_s x_s[n] Re(sum_k G_X e^{+2 pi i n k/N}) + y_s[n] Re(sum_k G_Y e^{+...}),
+// the real inverse transforms of the Hermitian extensions of G_X and G_Y, taken together
+// as one complex inverse transform of H_X + i H_Y.  Segments are transformed again in the
+// adjoint pass, not stored.
+//
+// Kernels (no atomics; every sum has a fixed order, so runs are bitwise reproducible):
+//   k_adj_forward  a grid of G CTAs, each over segments b, b + G, ...: decode, window, a
+//                  radix-16 Stockham transform of the pair x + i y in shared memory, split
+//                  into X and Y, per-CTA partial sums of |X|^2, |Y|^2, X conj(Y)
+//   k_adj_bins     per bin: partials summed (fp32 slices, added in fp64), the model,
+//                  Stokes and loss in fp64, the gain and leakage gradients and the
+//                  window-adjoint matrix in fp32
+//   k_adj_finish   block partials of the loss and gain gradients summed in order
+//   k_adj_window   per segment again: forward transform, G_X and G_Y, inverse transform,
+//                  per-CTA partials of the window gradient
+//   k_adj_wsum     the window-gradient partials summed per tap
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
@@ -35,182 +54,327 @@
 
 namespace polaris {
 
-constexpr int kAdjThreads = 1024;
+constexpr int kMaxCtasPerSm = 8;
 
 struct AdjArgs {
   const uint32_t* in[2];  // the two IFs' packed words
-  int N, log2n, nbin, nseg;
-  const float2* tw;       // W_N^j, j < N/2
+  int N, log2n, nbin, nseg, grid, threads;
+  const float2* tw;       // per-pass twiddles: tw[r Ns + k - 1] = W_{Ns R}^{r k} (N - 1 entries)
   const float* window;    // N
-  const float* gains;     // gR re, gR im, gL re, gL im
-  const float* leak;      // DR then DL, nbin (re, im) each
-  double* acc;            // RR, LL, RL re, RL im (4 x nbin)
-  const float4* res;      // per bin (a, b, c re, c im)
-  float* grad_w;          // N
-  float* grad_leak;       // 2 x nbin x 2
-  double* grad_g;         // 4
+  float* part;            // [grid][4][nbin]: |X|^2, |Y|^2, Re X conj(Y), Im X conj(Y)
+  const float4* mat;      // per bin (m11, m12), (m21, m22)
+  float* gpart;           // [grid][N] window-gradient partials
 };
 
-__device__ __forceinline__ float2 c_mul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
+// shared-memory layout of the N points: one float2 of padding after every 16 keeps the
+// stride-16 writes of the first pass, and every other access, free of bank conflicts
+__host__ __device__ __forceinline__ int apad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int adj_smem_points(int N) { return N + N / 16; }
+
 __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 c_scale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
 
-__device__ __forceinline__ unsigned bitrev_n(unsigned v, int log2n) { return __brev(v) >> (32 - log2n); }
-
-template <int BITS>
-__device__ __forceinline__ float adj_level(const uint32_t* words, long long n) {
-  constexpr int SPW = 32 / BITS;
-  return decode_level<BITS>(words[n / SPW], (uint32_t)((n % SPW) * BITS));
-}
-
-// in-place radix-2 DIT over z (input in bit-reversed order, output natural); sign -1 forward
-__device__ void adj_fft(float2* z, int N, const float2* tw, bool inverse) {
-  for (int half = 1; half < N; half <<= 1) {
-    const int step = N / (2 * half);
-    for (int b = threadIdx.x; b < N / 2; b += kAdjThreads) {
-      const int j = b & (half - 1);
-      const int base = ((b / half) * 2 * half) + j;
-      float2 w = __ldg(tw + j * step);
-      if (inverse) w.y = -w.y;
-      const float2 u = z[base], v = c_mul(z[base + half], w);
-      z[base] = c_add(u, v);
-      z[base + half] = make_float2(u.x - v.x, u.y - v.y);
+// One Stockham autosort pass of radix R (Ns = product of the radices already applied), in
+// place in z: every j < N/R reads z[j + r N/R] (r < R), multiplies by W_{Ns R}^{r (j mod Ns)}
+// (from the pass's own table, where consecutive j read consecutive entries),
+// takes an R-point DFT and writes output q to z[(j / Ns) Ns R + q Ns + j mod Ns].  All reads
+// of the pass finish before any write.  The block has exactly T = N/16 threads and each
+// holds 16 points: one j for R = 16, j = t, t + T, ... for smaller radices, always < N/R
+// (a bounds test here would push the point arrays into local memory).
+template <int R>
+__device__ __forceinline__ void stockham_pass(float2* z, int N, int Ns, const float2* __restrict__ tw, int T) {
+  constexpr int JPT = 16 / R;
+  const int m = N / R;
+  float2 v[JPT][R];
+#pragma unroll
+  for (int q = 0; q < JPT; ++q) {
+    const int j = threadIdx.x + q * T;
+    const int k = j & (Ns - 1);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float2 a = z[apad(j + r * m)];
+      if (r > 0 && Ns > 1) a = cmul(a, __ldg(tw + r * Ns + k - 1));
+      v[q][ct::bitrev(r, R)] = a;
     }
-    __syncthreads();
-  }
-}
-
-// MODE 0: accumulate RR, LL, RL.  MODE 1: adjoint (gain, leakage and window gradients).
-template <int BITS, int MODE>
-__global__ void __launch_bounds__(kAdjThreads) k_adj_segment(AdjArgs a) {
-  extern __shared__ float2 z[];
-  __shared__ double red[4][kAdjThreads / 32];
-  const int N = a.N, nbin = a.nbin, s = blockIdx.x;
-  const long long n0 = (long long)s * N;
-  // windowed levels of the pair as z = w (x + i y), in bit-reversed order
-  for (int n = threadIdx.x; n < N; n += kAdjThreads) {
-    const float wn = __ldg(a.window + n);
-    z[bitrev_n((unsigned)n, a.log2n)] =
-        make_float2(wn * adj_level<BITS>(a.in[0], n0 + n), wn * adj_level<BITS>(a.in[1], n0 + n));
   }
   __syncthreads();
-  adj_fft(z, N, a.tw, false);
-  const float2 gR = make_float2(__ldg(a.gains + 0), __ldg(a.gains + 1));
-  const float2 gL = make_float2(__ldg(a.gains + 2), __ldg(a.gains + 3));
-  double gg[4] = {0.0, 0.0, 0.0, 0.0};
-  // one thread per bin pair (k, N - k): both are read before either is rewritten
-  for (int k = threadIdx.x; k < nbin; k += kAdjThreads) {
-    const int km = (N - k) & (N - 1);
-    const float2 Zk = z[k], Zm = c_conj(z[km]);
-    const float2 X = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y + Zm.y));
-    const float2 Y = make_float2(0.5f * (Zk.y - Zm.y), -0.5f * (Zk.x - Zm.x));  // (Zk - Zm) / 2i
-    const float2 DR = make_float2(__ldg(a.leak + 2 * k), __ldg(a.leak + 2 * k + 1));
-    const float2 DL = make_float2(__ldg(a.leak + 2 * (nbin + k)), __ldg(a.leak + 2 * (nbin + k) + 1));
-    const float2 uR = c_add(X, c_mul(DR, Y)), uL = c_add(Y, c_mul(DL, X));
-    const float2 Xt = c_mul(gR, uR), Yt = c_mul(gL, uL);
-    if constexpr (MODE == 0) {
-      const float2 rl = c_mul(Xt, c_conj(Yt));
-      atomicAdd(a.acc + k, (double)Xt.x * Xt.x + (double)Xt.y * Xt.y);
-      atomicAdd(a.acc + nbin + k, (double)Yt.x * Yt.x + (double)Yt.y * Yt.y);
-      atomicAdd(a.acc + 2 * nbin + k, (double)rl.x);
-      atomicAdd(a.acc + 3 * nbin + k, (double)rl.y);
-    } else {
-      const float4 r = __ldg(a.res + k);  // a, b, c
-      const float2 c = make_float2(r.z, r.w);
-      const float2 GXt = c_add(c_scale(Xt, 2.f * r.x), c_mul(c, Yt));
-      const float2 GYt = c_add(c_scale(Yt, 2.f * r.y), c_mul(c_conj(c), Xt));
-      const float2 GX = c_add(c_mul(c_conj(gR), GXt), c_mul(c_conj(c_mul(gL, DL)), GYt));
-      const float2 GY = c_add(c_mul(c_conj(c_mul(gR, DR)), GXt), c_mul(c_conj(gL), GYt));
-      const float2 ggR = c_mul(c_conj(uR), GXt), ggL = c_mul(c_conj(uL), GYt);
-      gg[0] += ggR.x;
-      gg[1] += ggR.y;
-      gg[2] += ggL.x;
-      gg[3] += ggL.y;
-      const float2 gDR = c_mul(c_conj(c_mul(gR, Y)), GXt), gDL = c_mul(c_conj(c_mul(gL, X)), GYt);
-      atomicAdd(a.grad_leak + 2 * k, gDR.x);
-      atomicAdd(a.grad_leak + 2 * k + 1, gDR.y);
-      atomicAdd(a.grad_leak + 2 * (nbin + k), gDL.x);
-      atomicAdd(a.grad_leak + 2 * (nbin + k) + 1, gDL.y);
-      // Hermitian extensions of G_X, G_Y packed as H_X + i H_Y
-      if (k == 0 || k == N / 2) {
-        z[k] = make_float2(GX.x, GY.x);  // Re(G) at the self-mirrored bins
-      } else {
-        const float2 hx = c_scale(GX, 0.5f), hy = c_scale(GY, 0.5f);
-        z[k] = make_float2(hx.x - hy.y, hx.y + hy.x);    // hx + i hy
-        z[km] = make_float2(hx.x + hy.y, -hx.y + hy.x);  // conj(hx) + i conj(hy)
-      }
-    }
-  }
-  if constexpr (MODE == 1) {
-    // gain gradients: block sum, one double atomic per component
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      double v = gg[q];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if ((threadIdx.x & 31) == 0) red[q][threadIdx.x >> 5] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 4) {
-      double t = 0.0;
-      for (int w = 0; w < kAdjThreads / 32; ++w) t += red[threadIdx.x][w];
-      atomicAdd(a.grad_g + threadIdx.x, t);
-    }
-    // bit-reverse in place, inverse transform, then the window gradient
-    for (int i = threadIdx.x; i < N; i += kAdjThreads) {
-      const int j = (int)bitrev_n((unsigned)i, a.log2n);
-      if (i < j) {
-        const float2 t = z[i];
-        z[i] = z[j];
-        z[j] = t;
-      }
-    }
-    __syncthreads();
-    adj_fft(z, N, a.tw, true);
-    for (int n = threadIdx.x; n < N; n += kAdjThreads) {
-      const float2 v = z[n];
-      atomicAdd(a.grad_w + n, adj_level<BITS>(a.in[0], n0 + n) * v.x + adj_level<BITS>(a.in[1], n0 + n) * v.y);
-    }
+  for (int q = 0; q < JPT; ++q) {
+    const int j = threadIdx.x + q * T;
+    dit<R>(v[q]);
+    const int k = j & (Ns - 1);
+    const int base = (j - k) * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) z[apad(base + r * Ns)] = v[q][r];
+  }
+  __syncthreads();
+}
+
+// forward DFT of the N points in z (natural order in and out); callers sync before
+__device__ __forceinline__ void adj_fft(float2* z, int N, int log2n, const float2* __restrict__ tw, int T) {
+  int Ns = 1;
+#pragma unroll 1
+  for (int p = 0; p < (log2n >> 2); ++p, Ns <<= 4) stockham_pass<16>(z, N, Ns, tw, T);
+  switch (log2n & 3) {
+    case 1: stockham_pass<2>(z, N, Ns, tw, T); break;
+    case 2: stockham_pass<4>(z, N, Ns, tw, T); break;
+    case 3: stockham_pass<8>(z, N, Ns, tw, T); break;
+    default: break;
   }
 }
 
-// per bin: Stokes, residual coefficients (a, b, c), loss
-__global__ void k_adj_residual(const double* acc, const float* target, int nbin, float* stokes, float4* res,
-                               double* loss) {
-  __shared__ double red[8];
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  double l = 0.0;
+// level of sample idx of one IF
+template <int BITS>
+__device__ __forceinline__ float adj_level(const uint32_t* __restrict__ in, long long idx) {
+  if constexpr (BITS == 8) {
+    return (float)(int)__ldg(reinterpret_cast<const signed char*>(in) + idx);
+  } else {
+    constexpr int SPW = 32 / BITS;
+    return decode_level<BITS>(__ldg(in + idx / SPW), (uint32_t)(idx % SPW) * BITS);
+  }
+}
+
+// z[n] = w[n] (x[n] + i y[n]) for segment s; thread t fills n = t + T e, e < 16, so that
+// every load is coalesced and the stores are conflict-free
+template <int BITS>
+__device__ __forceinline__ void adj_load_segment(const AdjArgs& a, float2* z, long long s) {
+  const long long base = s * a.N;
+#pragma unroll 8
+  for (int e = 0; e < 16; ++e) {
+    const int n = threadIdx.x + e * a.threads;
+    const float w = __ldg(a.window + n);
+    z[apad(n)] = make_float2(w * adj_level<BITS>(a.in[0], base + n), w * adj_level<BITS>(a.in[1], base + n));
+  }
+}
+
+// one segment of the forward pass
+template <int BITS>
+__device__ __forceinline__ void adj_forward_segment(const AdjArgs& a, float2* z, long long s, bool first) {
+  const int N = a.N, nbin = a.nbin;
+  float* part = a.part + (size_t)blockIdx.x * 4 * nbin;
+  adj_load_segment<BITS>(a, z, s);
+  __syncthreads();
+  adj_fft(z, N, a.log2n, a.tw, a.threads);
+  // X = (Z[k] + conj Z[N-k]) / 2, Y = (Z[k] - conj Z[N-k]) / 2i
+#pragma unroll 1
+  for (int k = threadIdx.x; k < nbin; k += a.threads) {
+    const float2 Zk = z[apad(k)], Zm = c_conj(z[apad((N - k) & (N - 1))]);
+    const float2 X = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y + Zm.y));
+    const float2 Y = make_float2(0.5f * (Zk.y - Zm.y), -0.5f * (Zk.x - Zm.x));
+    float v[4] = {fmaf(X.x, X.x, X.y * X.y), fmaf(Y.x, Y.x, Y.y * Y.y), fmaf(X.x, Y.x, X.y * Y.y),
+                  fmaf(X.y, Y.x, -X.x * Y.y)};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) part[q * nbin + k] = first ? v[q] : part[q * nbin + k] + v[q];
+  }
+  __syncthreads();
+}
+
+template <int BITS>
+__global__ void __launch_bounds__(1024) k_adj_forward(AdjArgs a) {
+  extern __shared__ float2 z[];
+#pragma unroll 1
+  for (long long s = blockIdx.x; s < a.nseg; s += a.grid) adj_forward_segment<BITS>(a, z, s, s == blockIdx.x);
+}
+
+// one segment of the window-gradient pass
+template <int BITS>
+__device__ __forceinline__ void adj_window_segment(const AdjArgs& a, float2* z, long long s, bool first) {
+  const int N = a.N, nbin = a.nbin;
+  float* gpart = a.gpart + (size_t)blockIdx.x * N;
+  adj_load_segment<BITS>(a, z, s);
+  __syncthreads();
+  adj_fft(z, N, a.log2n, a.tw, a.threads);
+  // G_X, G_Y per bin pair; conj of the Hermitian extension of G_X + i G_Y goes back into z
+  // (the inverse transform is conj(DFT(conj H))).  Thread k owns slots k and N - k.
+#pragma unroll 1
+  for (int k = threadIdx.x; k < nbin; k += a.threads) {
+    const int km = (N - k) & (N - 1);
+    const float2 Zk = z[apad(k)], Zm = c_conj(z[apad(km)]);
+    const float2 X = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y + Zm.y));
+    const float2 Y = make_float2(0.5f * (Zk.y - Zm.y), -0.5f * (Zk.x - Zm.x));
+    const float4 r0 = __ldg(a.mat + 2 * k), r1 = __ldg(a.mat + 2 * k + 1);
+    const float2 GX = c_add(cmul(make_float2(r0.x, r0.y), X), cmul(make_float2(r0.z, r0.w), Y));
+    const float2 GY = c_add(cmul(make_float2(r1.x, r1.y), X), cmul(make_float2(r1.z, r1.w), Y));
+    if (k == 0 || 2 * k == N) {
+      z[apad(k)] = make_float2(GX.x, -GY.x);  // H = Re G_X + i Re G_Y
+    } else {
+      const float2 hx = make_float2(0.5f * GX.x, 0.5f * GX.y), hy = make_float2(0.5f * GY.x, 0.5f * GY.y);
+      // H[k] = hx + i hy, H[N-k] = conj(hx) + i conj(hy); store their conjugates
+      z[apad(k)] = make_float2(hx.x - hy.y, -(hx.y + hy.x));
+      z[apad(km)] = make_float2(hx.x + hy.y, hx.y - hy.x);
+    }
+  }
+  __syncthreads();
+  adj_fft(z, N, a.log2n, a.tw, a.threads);
+  // h = conj(F): dL/dw[n] += x[n] Re h[n] + y[n] Im h[n] = x F.x - y F.y
+  const long long base = s * N;
+#pragma unroll 8
+  for (int e = 0; e < 16; ++e) {
+    const int n = threadIdx.x + e * a.threads;
+    const float2 F = z[apad(n)];
+    const float g = fmaf(adj_level<BITS>(a.in[0], base + n), F.x, -adj_level<BITS>(a.in[1], base + n) * F.y);
+    gpart[n] = first ? g : gpart[n] + g;
+  }
+  __syncthreads();
+}
+
+template <int BITS>
+__global__ void __launch_bounds__(1024) k_adj_window(AdjArgs a) {
+  extern __shared__ float2 z[];
+#pragma unroll 1
+  for (long long s = blockIdx.x; s < a.nseg; s += a.grid) adj_window_segment<BITS>(a, z, s, s == blockIdx.x);
+}
+
+struct dc {
+  double x, y;
+};
+__device__ __forceinline__ dc dmul(dc a, dc b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ dc dconj(dc a) { return {a.x, -a.y}; }
+__device__ __forceinline__ dc dadd(dc a, dc b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ dc dscale(dc a, double s) { return {a.x * s, a.y * s}; }
+__device__ __forceinline__ double dnorm(dc a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ float2 fscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float fnorm(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+
+struct BinArgs {
+  const float* part;
+  int grid, nbin;
+  const float* gains;
+  const float* leak;
+  const float* target;
+  float* stokes;
+  float* grad_leak;
+  float4* mat;
+  double* bpart;  // [blocks][5]: loss, G_gR re/im, G_gL re/im
+};
+
+// A block covers kBinsPerBlock bins; its kSlices warps sum the per-CTA partials of the
+// segment kernel over interleaved slices of CTAs in fp32 (many loads in flight), the slice
+// sums are added in fp64 in slice order, then one warp evaluates the model per bin: the
+// sums, Stokes and loss in fp64, the gradients and the window-adjoint matrix in fp32.
+constexpr int kBinsPerBlock = 32, kSlices = 8;
+
+__global__ void __launch_bounds__(kBinsPerBlock * kSlices) k_adj_bins(BinArgs a) {
+  __shared__ float red[kSlices][4][kBinsPerBlock];
+  const int nbin = a.nbin;
+  const int lane = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int k = blockIdx.x * kBinsPerBlock + lane;
+  float s4[4] = {0.f, 0.f, 0.f, 0.f};
   if (k < nbin) {
-    const double RR = acc[k], LL = acc[nbin + k];
-    const double S[4] = {0.5 * (RR + LL), acc[2 * nbin + k], acc[3 * nbin + k], 0.5 * (RR - LL)};
-    if (stokes)
-      for (int q = 0; q < 4; ++q) stokes[q * nbin + k] = (float)S[q];
-    if (target) {
-      double r[4];
-      for (int q = 0; q < 4; ++q) {
-        const double d = S[q] - (double)target[q * nbin + k];
-        l += d * d;
-        r[q] = 2.0 * d;
-      }
-      res[k] = make_float4((float)(0.5 * (r[0] + r[3])), (float)(0.5 * (r[0] - r[3])), (float)r[1], (float)r[2]);
+#pragma unroll 4
+    for (int g = sl; g < a.grid; g += kSlices) {
+      const float* p = a.part + (size_t)g * 4 * nbin + k;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) s4[q] += __ldcg(p + q * nbin);
     }
   }
-  if (loss) {
-    for (int o = 16; o > 0; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-      atomicAdd(loss, t);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) red[sl][q][lane] = s4[q];
+  __syncthreads();
+  if (sl != 0) return;
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  if (k < nbin) {
+    double t4[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int w = 0; w < kSlices; ++w)
+      for (int q = 0; q < 4; ++q) t4[q] += (double)red[w][q][lane];
+    const double A = t4[0], B = t4[1];
+    const dc C = {t4[2], t4[3]};
+    const dc gR = {a.gains[0], a.gains[1]}, gL = {a.gains[2], a.gains[3]};
+    const dc DR = {a.leak[2 * k], a.leak[2 * k + 1]};
+    const dc DL = {a.leak[2 * (nbin + k)], a.leak[2 * (nbin + k) + 1]};
+    const double PR = A + dnorm(DR) * B + 2.0 * dmul(dconj(DR), C).x;
+    const double PL = B + dnorm(DL) * A + 2.0 * dmul(DL, C).x;
+    const dc Qm = dadd(dadd(C, dscale(dconj(DL), A)), dadd(dscale(DR, B), dmul(dmul(DR, dconj(DL)), dconj(C))));
+    const double RR = dnorm(gR) * PR, LL = dnorm(gL) * PL;
+    const dc RL = dmul(dmul(gR, dconj(gL)), Qm);
+    const double S[4] = {0.5 * (RR + LL), RL.x, RL.y, 0.5 * (RR - LL)};
+    if (a.stokes)
+      for (int q = 0; q < 4; ++q) a.stokes[q * nbin + k] = (float)S[q];
+    if (a.target) {
+      float r[4];
+      for (int q = 0; q < 4; ++q) {
+        const double d = S[q] - (double)a.target[q * nbin + k];
+        acc[0] += d * d;
+        r[q] = (float)(2.0 * d);
+      }
+      if (a.mat) {
+        const float ca = 0.5f * (r[0] + r[3]), cb = 0.5f * (r[0] - r[3]);
+        const float2 c = make_float2(r[1], r[2]), cc = c_conj(c);
+        const float2 fgR = make_float2(a.gains[0], a.gains[1]), fgL = make_float2(a.gains[2], a.gains[3]);
+        const float2 fDR = make_float2((float)DR.x, (float)DR.y), fDL = make_float2((float)DL.x, (float)DL.y);
+        const float2 fC = make_float2((float)C.x, (float)C.y), fQ = make_float2((float)Qm.x, (float)Qm.y);
+        const float fA = (float)A, fB = (float)B;
+        const float2 ggR = c_add(fscale(fgR, 2.f * ca * (float)PR), cmul(cmul(c, fgL), c_conj(fQ)));
+        const float2 ggL = c_add(fscale(fgL, 2.f * cb * (float)PL), cmul(cmul(cc, fgR), fQ));
+        acc[1] = ggR.x;
+        acc[2] = ggR.y;
+        acc[3] = ggL.x;
+        acc[4] = ggL.y;
+        const float2 gDR = c_add(fscale(c_add(fscale(fDR, fB), fC), 2.f * ca * fnorm(fgR)),
+                                 cmul(cmul(c, cmulc(fgR, fgL)), c_add(make_float2(fB, 0.f), cmul(fDL, fC))));
+        const float2 gDL = c_add(fscale(c_add(fscale(fDL, fA), c_conj(fC)), 2.f * cb * fnorm(fgL)),
+                                 cmul(cmul(cc, cmulc(fgL, fgR)), c_add(make_float2(fA, 0.f), cmul(fDR, c_conj(fC)))));
+        a.grad_leak[2 * k] = gDR.x;
+        a.grad_leak[2 * k + 1] = gDR.y;
+        a.grad_leak[2 * (nbin + k)] = gDL.x;
+        a.grad_leak[2 * (nbin + k) + 1] = gDL.y;
+        // G_Xt = al1 X + be1 Y, G_Yt = al2 X + be2 Y; G_X = conj(gR) G_Xt + conj(gL DL) G_Yt,
+        // G_Y = conj(gR DR) G_Xt + conj(gL) G_Yt
+        const float2 gLDL = cmul(fgL, fDL), gRDR = cmul(fgR, fDR);
+        const float2 al1 = c_add(fscale(fgR, 2.f * ca), cmul(c, gLDL));
+        const float2 be1 = c_add(fscale(gRDR, 2.f * ca), cmul(c, fgL));
+        const float2 al2 = c_add(fscale(gLDL, 2.f * cb), cmul(cc, fgR));
+        const float2 be2 = c_add(fscale(fgL, 2.f * cb), cmul(cc, gRDR));
+        const float2 m11 = c_add(cmulc(fgR, al1), cmulc(gLDL, al2)), m12 = c_add(cmulc(fgR, be1), cmulc(gLDL, be2));
+        const float2 m21 = c_add(cmulc(gRDR, al1), cmulc(fgL, al2)), m22 = c_add(cmulc(gRDR, be1), cmulc(fgL, be2));
+        a.mat[2 * k] = make_float4(m11.x, m11.y, m12.x, m12.y);
+        a.mat[2 * k + 1] = make_float4(m21.x, m21.y, m22.x, m22.y);
+      }
+    }
+  }
+  if (a.bpart) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      double v = acc[q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) a.bpart[5 * blockIdx.x + q] = v;
     }
   }
 }
 
-__global__ void k_adj_gains_out(const double* g, float* out) {
-  if (threadIdx.x < 4) out[threadIdx.x] = (float)g[threadIdx.x];
+// five warps, one per quantity: block partials summed lane-strided, then across the warp
+__global__ void __launch_bounds__(160) k_adj_finish(const double* bpart, int blocks, double* loss, float* grad_gains) {
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double t = 0.0;
+  for (int b = lane; b < blocks; b += 32) t += bpart[5 * b + q];
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if (lane == 0) {
+    if (q == 0) {
+      if (loss) *loss = t;
+    } else if (grad_gains) {
+      grad_gains[q - 1] = (float)t;
+    }
+  }
+}
+
+// window-gradient partials summed per tap: 32 taps per block, kSlices warps over the CTAs
+__global__ void __launch_bounds__(kBinsPerBlock * kSlices) k_adj_wsum(const float* gpart, int grid, int N,
+                                                                      float* grad_w) {
+  __shared__ float red[kSlices][kBinsPerBlock];
+  const int lane = threadIdx.x & 31, sl = threadIdx.x >> 5;
+  const int n = blockIdx.x * kBinsPerBlock + lane;
+  float t = 0.f;
+  if (n < N) {
+#pragma unroll 4
+    for (int g = sl; g < grid; g += kSlices) t += __ldcg(gpart + (size_t)g * N + n);
+  }
+  red[sl][lane] = t;
+  __syncthreads();
+  if (sl == 0 && n < N) {
+    double u = 0.0;
+    for (int w = 0; w < kSlices; ++w) u += (double)red[w][lane];
+    grad_w[n] = (float)u;
+  }
 }
 
 }  // namespace polaris
@@ -218,10 +382,13 @@ __global__ void k_adj_gains_out(const double* g, float* out) {
 using namespace polaris;
 
 struct polaris_adj {
-  int N = 0, log2n = 0, nbin = 0, bits = 0, device = 0;
+  int N = 0, log2n = 0, nbin = 0, bits = 0, device = 0, threads = 0, grid_max = 0, bin_blocks = 0;
+  size_t smem = 0;
   float2* d_tw = nullptr;
-  double* d_acc = nullptr;  // 4 x nbin, then 4 gain-gradient doubles
-  float4* d_res = nullptr;
+  float* d_part = nullptr;   // [grid_max][4][nbin]
+  float* d_gpart = nullptr;  // [grid_max][N]
+  float4* d_mat = nullptr;   // [nbin][2]
+  double* d_bpart = nullptr; // [bin_blocks][5]
   std::string err;
 };
 
@@ -232,6 +399,27 @@ static int adj_err(polaris_adj* h, int code, const char* msg, const char* detail
   if (h) h->err = m;
   else g_adj_create_err = m;
   return code;
+}
+
+template <int BITS>
+static cudaError_t adj_prepare(polaris_adj* h, int* ctas_per_sm) {
+  const int smem = (int)h->smem;
+  cudaError_t e = cudaFuncSetAttribute(k_adj_forward<BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_window<BITS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int o1 = 0, o2 = 0;
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k_adj_forward<BITS>, h->threads, h->smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o2, k_adj_window<BITS>, h->threads, h->smem);
+  *ctas_per_sm = std::min(o1, o2);
+  return e;
+}
+
+static void adj_free(polaris_adj* h) {
+  cudaFree(h->d_tw);
+  cudaFree(h->d_part);
+  cudaFree(h->d_gpart);
+  cudaFree(h->d_mat);
+  cudaFree(h->d_bpart);
 }
 
 extern "C" int polaris_adj_create(int64_t n_fft, int bits, int device, polaris_adj** out) {
@@ -252,27 +440,57 @@ extern "C" int polaris_adj_create(int64_t n_fft, int bits, int device, polaris_a
   h->nbin = h->N / 2 + 1;
   h->bits = bits;
   h->device = device;
+  h->threads = h->N / 16;
+  h->smem = (size_t)adj_smem_points(h->N) * sizeof(float2);
+  h->bin_blocks = (h->nbin + kBinsPerBlock - 1) / kBinsPerBlock;
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(device);
-  std::vector<float2> tw(h->N / 2);
-  for (int j = 0; j < h->N / 2; ++j) {
-    const double ang = -2.0 * M_PI * (double)j / (double)h->N;
-    tw[j] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+  int nsm = 0, occ = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) {
+    switch (bits) {
+      case 1: e = adj_prepare<1>(h, &occ); break;
+      case 2: e = adj_prepare<2>(h, &occ); break;
+      case 4: e = adj_prepare<4>(h, &occ); break;
+      default: e = adj_prepare<8>(h, &occ); break;
+    }
+  }
+  if (e != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    cudaSetDevice(prev);
+    delete h;
+    return adj_err(nullptr, POLARIS_ECUDA, "adjoint kernels cannot be launched: ",
+                   e != cudaSuccess ? cudaGetErrorString(e) : "zero occupancy");
+  }
+  h->grid_max = nsm * std::min(occ, kMaxCtasPerSm);
+  // per-pass twiddles of the Stockham passes (radix 16, then 2, 4 or 8): pass with Ns
+  // points done and radix R keeps W_{Ns R}^{r k} at r Ns + k - 1 (1 <= r < R, k < Ns); the
+  // offsets Ns - 1 telescope, so the N - 1 entries tile [0, N - 1) exactly
+  std::vector<float2> tw(h->N);
+  for (int Ns = 1; Ns < h->N;) {
+    const int R = std::min(16, h->N / Ns);
+    for (int r = 1; r < R; ++r)
+      for (int k = 0; k < Ns; ++k) {
+        const double ang = -2.0 * M_PI * (double)r * (double)k / (double)(Ns * R);
+        tw[r * Ns + k - 1] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+      }
+    Ns *= R;
   }
   bool ok = cudaMalloc((void**)&h->d_tw, tw.size() * sizeof(float2)) == cudaSuccess &&
-            cudaMalloc((void**)&h->d_acc, (4 * (size_t)h->nbin + 4) * sizeof(double)) == cudaSuccess &&
-            cudaMalloc((void**)&h->d_res, (size_t)h->nbin * sizeof(float4)) == cudaSuccess &&
+            cudaMalloc((void**)&h->d_part, (size_t)h->grid_max * 4 * h->nbin * sizeof(float)) == cudaSuccess &&
+            cudaMalloc((void**)&h->d_gpart, (size_t)h->grid_max * h->N * sizeof(float)) == cudaSuccess &&
+            cudaMalloc((void**)&h->d_mat, (size_t)h->nbin * 2 * sizeof(float4)) == cudaSuccess &&
+            cudaMalloc((void**)&h->d_bpart, (size_t)h->bin_blocks * 5 * sizeof(double)) == cudaSuccess &&
             cudaMemcpy(h->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice) == cudaSuccess;
-  cudaSetDevice(prev);
   if (!ok) {
     cudaGetLastError();
-    cudaFree(h->d_tw);
-    cudaFree(h->d_acc);
-    cudaFree(h->d_res);
+    adj_free(h);
+    cudaSetDevice(prev);
     delete h;
     return adj_err(nullptr, POLARIS_ENOMEM, "device allocation failed");
   }
+  cudaSetDevice(prev);
   *out = h;
   return POLARIS_OK;
 }
@@ -282,9 +500,7 @@ extern "C" void polaris_adj_destroy(polaris_adj* h) {
   int prev = 0;
   cudaGetDevice(&prev);
   cudaSetDevice(h->device);
-  cudaFree(h->d_tw);
-  cudaFree(h->d_acc);
-  cudaFree(h->d_res);
+  adj_free(h);
   cudaSetDevice(prev);
   delete h;
 }
@@ -294,18 +510,19 @@ extern "C" const char* polaris_adj_last_error(const polaris_adj* h) {
 }
 
 template <int BITS>
-static cudaError_t adj_launch(const AdjArgs& a, bool grads, cudaStream_t st) {
-  const size_t smem = (size_t)a.N * sizeof(float2);
-  cudaError_t e = cudaFuncSetAttribute(k_adj_segment<BITS, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adj_segment<BITS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  if (!grads) {
-    k_adj_segment<BITS, 0><<<a.nseg, kAdjThreads, smem, st>>>(a);
-  } else {
-    k_adj_segment<BITS, 1><<<a.nseg, kAdjThreads, smem, st>>>(a);
-  }
+static cudaError_t adj_segments(const AdjArgs& a, size_t smem, bool window_pass, cudaStream_t st) {
+  if (!window_pass) k_adj_forward<BITS><<<a.grid, a.threads, smem, st>>>(a);
+  else k_adj_window<BITS><<<a.grid, a.threads, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+static cudaError_t adj_segments_bits(int bits, const AdjArgs& a, size_t smem, bool window_pass, cudaStream_t st) {
+  switch (bits) {
+    case 1: return adj_segments<1>(a, smem, window_pass, st);
+    case 2: return adj_segments<2>(a, smem, window_pass, st);
+    case 4: return adj_segments<4>(a, smem, window_pass, st);
+    default: return adj_segments<8>(a, smem, window_pass, st);
+  }
 }
 
 extern "C" int polaris_adj_run(polaris_adj* h, const void* const* packed, int64_t n_samples, const float* window,
@@ -326,51 +543,45 @@ extern "C" int polaris_adj_run(polaris_adj* h, const void* const* packed, int64_
   cudaGetDevice(&prev);
   cudaSetDevice(h->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
-  const int nbin = h->nbin;
   AdjArgs a;
   memset(&a, 0, sizeof a);
   a.in[0] = static_cast<const uint32_t*>(packed[0]);
   a.in[1] = static_cast<const uint32_t*>(packed[1]);
   a.N = h->N;
   a.log2n = h->log2n;
-  a.nbin = nbin;
+  a.nbin = h->nbin;
   a.nseg = (int)(n_samples / h->N);
+  a.grid = std::min(a.nseg, h->grid_max);
+  a.threads = h->threads;
   a.tw = h->d_tw;
   a.window = window;
-  a.gains = gains;
-  a.leak = leak;
-  a.acc = h->d_acc;
-  a.res = h->d_res;
-  a.grad_w = grad_window;
-  a.grad_leak = grad_leak;
-  a.grad_g = h->d_acc + 4 * (size_t)nbin;
-  cudaError_t e = cudaMemsetAsync(h->d_acc, 0, (4 * (size_t)nbin + 4) * sizeof(double), st);
-  if (e == cudaSuccess && loss) e = cudaMemsetAsync(loss, 0, sizeof(double), st);
+  a.part = h->d_part;
+  a.mat = h->d_mat;
+  a.gpart = h->d_gpart;
+  cudaError_t e = adj_segments_bits(h->bits, a, h->smem, false, st);
   if (e == cudaSuccess) {
-    switch (h->bits) {  // forward: accumulate RR, LL, RL
-      case 1: e = adj_launch<1>(a, false, st); break;
-      case 2: e = adj_launch<2>(a, false, st); break;
-      case 4: e = adj_launch<4>(a, false, st); break;
-      default: e = adj_launch<8>(a, false, st); break;
-    }
+    BinArgs b;
+    b.part = h->d_part;
+    b.grid = a.grid;
+    b.nbin = h->nbin;
+    b.gains = gains;
+    b.leak = leak;
+    b.target = target;
+    b.stokes = stokes;
+    b.grad_leak = grads ? grad_leak : nullptr;
+    b.mat = grads ? h->d_mat : nullptr;
+    b.bpart = (loss || grads) ? h->d_bpart : nullptr;
+    k_adj_bins<<<h->bin_blocks, kBinsPerBlock * kSlices, 0, st>>>(b);
+    e = cudaGetLastError();
   }
-  if (e == cudaSuccess) {
-    k_adj_residual<<<(nbin + 255) / 256, 256, 0, st>>>(h->d_acc, target, nbin, stokes, h->d_res, loss);
+  if (e == cudaSuccess && (loss || grads)) {
+    k_adj_finish<<<1, 160, 0, st>>>(h->d_bpart, h->bin_blocks, loss, grads ? grad_gains : nullptr);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && grads) {
-    e = cudaMemsetAsync(grad_window, 0, (size_t)h->N * sizeof(float), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(grad_leak, 0, 4 * (size_t)nbin * sizeof(float), st);
+    e = adj_segments_bits(h->bits, a, h->smem, true, st);
     if (e == cudaSuccess) {
-      switch (h->bits) {  // adjoint: transforms again, gradients
-        case 1: e = adj_launch<1>(a, true, st); break;
-        case 2: e = adj_launch<2>(a, true, st); break;
-        case 4: e = adj_launch<4>(a, true, st); break;
-        default: e = adj_launch<8>(a, true, st); break;
-      }
-    }
-    if (e == cudaSuccess) {
-      k_adj_gains_out<<<1, 32, 0, st>>>(a.grad_g, grad_gains);
+      k_adj_wsum<<<(h->N + kBinsPerBlock - 1) / kBinsPerBlock, kBinsPerBlock * kSlices, 0, st>>>(h->d_gpart, a.grid, h->N, grad_window);
       e = cudaGetLastError();
     }
   }

@@ -21,6 +21,11 @@ Workload recipes (the paper's observations are not available; these stand in):
     lines of FWHM 20 channels whose peak spectral density is 5x the continuum,
     at channels 16384 (unpolarised), 32768 (linearly polarised, chi = 30 deg)
     and 49152 (circularly polarised, Y lagging X by 90 deg).
+  * ``config_circular``: 2 circular-feed IFs (R, L), int8 (noise sigma = 20),
+    16384-point segments, 256 segments; unpolarised noise plus one Gaussian line
+    (FWHM 200 channels, peak 3x the continuum, at channel 3000) with fractional
+    Stokes q = 0.3, u = -0.2, v = 0.1 (in the circular basis <|R|^2> ~ I + V,
+    <|L|^2> ~ I - V, <R conj L> ~ Q + iU).
 """
 from __future__ import annotations
 
@@ -29,6 +34,7 @@ import numpy as np
 __all__ = [
     "samples_per_word", "pack", "unpack_codes", "quantize", "quantize_2bit", "quantize_int8",
     "quantize_1bit", "quantize_4bit", "config_tiny", "config_paper", "paper_block", "random_codes",
+    "config_circular",
 ]
 
 
@@ -174,3 +180,43 @@ def config_paper(seed: int = 1256, n_segments: int = 61, n_fft: int = 131072, n_
         sd = v.std()
         packed.append(pack(quantize(v / sd, bits), bits))
     return packed, dict(bits=bits, n_fft=n_fft, n_samples=n_segments * n_fft, window="rect")
+
+
+def config_circular(seed: int = 1412, n_fft: int = 16384, n_segments: int = 256, q: float = 0.3, u: float = -0.2,
+                    v: float = 0.1, line_peak: float = 3.0, center: float = 3000.0, fwhm: float = 200.0,
+                    sigma: float = 20.0):
+    """Two circular-feed IFs (R, L) as packed int8 streams: unpolarised noise plus a line
+    with fractional Stokes (q, u, v), synthesised per segment in the frequency domain
+    (generator only) from two independent complex Gaussian series S1, S2 per channel:
+    R = a S1, L = b S1 + c S2 with a = sqrt(1 + v), b = (q - iu) / a and
+    |c|^2 = 1 - v - |b|^2, so that <|R|^2> = 1 + v, <|L|^2> = 1 - v, <R conj L> = q + iu
+    per unit of line power.  Needs q^2 + u^2 + v^2 <= 1.
+    Returns (list of 2 packed uint32 arrays, dict of parameters)."""
+    if q * q + u * u + v * v > 1.0:
+        raise ValueError("fractional polarisation above 1")
+    rng = np.random.default_rng(seed)
+    nb = n_fft // 2 + 1
+    prof = line_peak * _gauss_profile(nb, center, fwhm)
+    a = np.sqrt(1.0 + v)
+    b = (q - 1j * u) / a
+    c = np.sqrt(max(0.0, 1.0 - v - abs(b) ** 2))
+
+    def cg(scale):
+        return (rng.standard_normal(nb) + 1j * rng.standard_normal(nb)) * np.sqrt(scale / 2.0)
+
+    rs, ls = [], []
+    for _ in range(n_segments):
+        s1, s2 = cg(prof), cg(prof)
+        fr = cg(1.0) + a * s1
+        fl = cg(1.0) + b * s1 + c * s2
+        for f in (fr, fl):
+            f[0] = f[0].real
+            f[-1] = f[-1].real
+        rs.append(np.fft.irfft(fr, n_fft))
+        ls.append(np.fft.irfft(fl, n_fft))
+    # one scale for both streams: separate normalisations would unbalance the continuum
+    xr, xl = np.concatenate(rs), np.concatenate(ls)
+    scale = sigma / np.sqrt(0.5 * (xr.var() + xl.var()))
+    packed = [pack(quantize_int8(x * scale), 8) for x in (xr, xl)]
+    return packed, dict(bits=8, n_fft=n_fft, n_samples=n_segments * n_fft, q=q, u=u, v=v, center=center,
+                        fwhm=fwhm, line_peak=line_peak, window="hann")

@@ -77,3 +77,22 @@ def test_gradient_matches_central_differences(orc):
     flat = gd.reshape(-1)
     for i in [0, 1, 5, 2 * (N // 2), 2 * (N // 2) + 1, 2 * (N // 2 + 1) + 9, 4 * (N // 2 + 1) - 1]:
         assert flat[i] == pytest.approx(_fd(loss_d, leak, i, 1e-4), rel=1e-3, abs=1e-6 * np.abs(flat).max())
+
+
+def test_circular_source_carries_its_fractional_stokes(orc):
+    """The differentiable workload's generator: with unit gains and no leakage, the line's
+    excess over the continuum has Q/I, U/I, V/I equal to the fractions it was built with
+    (a check of the input recipe, through the oracle's circular-feed Stokes)."""
+    packed, cfg = synth.config_circular(seed=3, n_fft=1024, n_segments=256, center=200.0, fwhm=60.0,
+                                        line_peak=4.0)
+    n_fft, n = cfg["n_fft"], cfg["n_samples"]
+    nb = n_fft // 2 + 1
+    st, _ = orc.leak_forward(packed, 8, n_fft, n, np.ones(n_fft), np.array([1.0, 0.0, 1.0, 0.0]),
+                             np.zeros((2, nb, 2)))
+    on = slice(185, 216)
+    off = np.r_[20:120, 300:500]
+    excess = st[:, on].sum(1) - st[:, off].mean(1) * (on.stop - on.start)
+    frac = excess[1:] / excess[0]
+    np.testing.assert_allclose(frac, [cfg["q"], cfg["u"], cfg["v"]], atol=0.02)
+    # off the line the source is unpolarised
+    assert np.abs(st[1:, off].mean(1)).max() < 0.02 * st[0, off].mean()
