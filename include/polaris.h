@@ -256,6 +256,42 @@ int polaris_adj_run(polaris_adj* h, const void* const* packed, int64_t n_samples
 void polaris_adj_destroy(polaris_adj* h);
 const char* polaris_adj_last_error(const polaris_adj* h);
 
+/* ---- Tensor-core DFT spectrometer (precision variant of the transform) ----
+ * The spectrometer's transform (Sec. 2: FFT of each segment, auto and cross products,
+ * accumulation; Stokes by Eq. 2) for one FFT pair of IFs, with the FFT taken as radix-64
+ * Stockham passes whose 64-point DFTs run as GEMMs on the tensor cores (tcgen05.mma,
+ * 16-bit operands, FP32 accumulation).  FP32 data are split into two 16-bit halves and
+ * multiplied as three products (the lo x lo term dropped):
+ *   POLARIS_TC_BF16X3  bf16 halves (about 17 significant bits)
+ *   POLARIS_TC_FP16X3  fp16 halves (about 22 bits), each DFT vector scaled by an exact
+ *                      power of two into fp16 range
+ *   POLARIS_TC_BF16X1  one bf16 product (the plain 16-bit tensor-core result)
+ * Twiddles and DFT matrices are FP64-computed; integration accumulators are FP64.
+ * polaris_tc_create: n_fft 4096 (= 64^2) or 262144 (= 64^3); bits 1/2/4/8; window
+ *   POLARIS_WIN_* (taps: n_fft floats for POLARIS_WIN_CUSTOM, copied); on `device`.
+ *   Holds about 70 MB of device memory (two 32 MB pass buffers).
+ * polaris_tc_feed: packed[2] are DEVICE pointers to the two IFs' packed streams (layout as
+ *   spectrometer_feed), n_samples each, a multiple of n_fft (whole segments, hop = n_fft);
+ *   queued on cuda_stream (NULL = legacy stream); accumulates.
+ * polaris_tc_integrate: writes DEVICE fp64 outputs (each may be NULL): autos [2][nbin],
+ *   cross [nbin][2] (X conj Y), stokes [4][nbin] (I, Q, U, V for linear feeds, psi = 0,
+ *   unit gains); nbin = n_fft/2 + 1; *n_segments (host) = segments integrated; clears the
+ *   accumulators; synchronises cuda_stream.  POLARIS_ETIMEOUT if a tensor-core completion
+ *   wait ran out (bounded; polaris_tc_set_wait_limit lowers the bound for tests, -1
+ *   restores it), after which the handle answers POLARIS_ESTATE.
+ * Errors: POLARIS_EINVAL (bad argument), POLARIS_ENOMEM, POLARIS_ECUDA; text from
+ * polaris_tc_last_error (NULL handle: the last failed create in this thread). */
+enum { POLARIS_TC_BF16X3 = 0, POLARIS_TC_FP16X3 = 1, POLARIS_TC_BF16X1 = 2 };
+typedef struct polaris_tc polaris_tc;
+int polaris_tc_create(int64_t n_fft, int bits, int window, const float* taps, int precision, int device,
+                      polaris_tc** out);
+int polaris_tc_feed(polaris_tc* h, const void* const* packed, int64_t n_samples, void* cuda_stream);
+int polaris_tc_integrate(polaris_tc* h, double* autos, double* cross, double* stokes, int64_t* n_segments,
+                         void* cuda_stream);
+int polaris_tc_set_wait_limit(polaris_tc* h, int64_t limit);
+void polaris_tc_destroy(polaris_tc* h);
+const char* polaris_tc_last_error(const polaris_tc* h);
+
 /* Bounded device-side waits.  Phase 2 (N >= 2^17) prefetches its next columns with
  * asynchronous bulk copies and waits for them on a shared-memory barrier; every such wait
  * polls at most a fixed number of times.  If one runs out, the kernel records the fact in

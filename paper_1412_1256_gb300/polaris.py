@@ -21,6 +21,7 @@ LIB_PATH = os.environ.get("POLARIS_LIB") or os.path.join(HERE, "libpolaris.so")
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT = 0, -1, -2, -3, -4, -5
 WIN_RECT, WIN_HANN, WIN_CUSTOM = 0, 1, 2
 FEED_LINEAR, FEED_CIRCULAR = 0, 1
+TC_BF16X3, TC_FP16X3, TC_BF16X1 = 0, 1, 2
 STATUS_NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ESTATE: "ESTATE", ETIMEOUT: "ETIMEOUT"}
 
 EXPORTS = (
@@ -30,6 +31,8 @@ EXPORTS = (
     "spectrometer_set_profiling", "spectrometer_kernel_times", "spectrometer_run_noalloc",
     "spectrometer_code_histogram", "polaris_power_from_histogram", "polaris_set_wait_limit",
     "polaris_adj_create", "polaris_adj_run", "polaris_adj_destroy", "polaris_adj_last_error",
+    "polaris_tc_create", "polaris_tc_feed", "polaris_tc_integrate", "polaris_tc_set_wait_limit",
+    "polaris_tc_destroy", "polaris_tc_last_error",
 )
 
 
@@ -105,6 +108,18 @@ def load(path: str = LIB_PATH):
             lib.polaris_adj_destroy.restype = None
             lib.polaris_adj_last_error.argtypes = [vp]
             lib.polaris_adj_last_error.restype = ctypes.c_char_p
+            lib.polaris_tc_create.argtypes = [i64, ci, ci, vp, ci, ci, ctypes.POINTER(vp)]
+            lib.polaris_tc_create.restype = ci
+            lib.polaris_tc_feed.argtypes = [vp, ctypes.POINTER(vp), i64, vp]
+            lib.polaris_tc_feed.restype = ci
+            lib.polaris_tc_integrate.argtypes = [vp, vp, vp, vp, ctypes.POINTER(i64), vp]
+            lib.polaris_tc_integrate.restype = ci
+            lib.polaris_tc_set_wait_limit.argtypes = [vp, i64]
+            lib.polaris_tc_set_wait_limit.restype = ci
+            lib.polaris_tc_destroy.argtypes = [vp]
+            lib.polaris_tc_destroy.restype = None
+            lib.polaris_tc_last_error.argtypes = [vp]
+            lib.polaris_tc_last_error.restype = ctypes.c_char_p
             lib.polaris_set_wait_limit.argtypes = [i64]
             lib.polaris_set_wait_limit.restype = None
             lib.spectrometer_code_histogram.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ci]
@@ -424,3 +439,70 @@ def leakage_loss(adj: "Adjoint", packed, n_samples: int, window, gains, leak, ta
             return s * gw, s * gg, s * gd
 
     return _LeakageLoss.apply(window, gains, leak)
+
+
+class TensorCoreSpectrometer:
+    """Tensor-core DFT spectrometer for one FFT pair (polaris_tc_*): the precision variant
+    of the transform, radix-64 DFTs as tcgen05 GEMMs with split 16-bit operands, FP64
+    accumulators.  Inputs are CUDA tensors of packed words; outputs are float64 tensors."""
+
+    PRECISIONS = {"bf16x3": TC_BF16X3, "fp16x3": TC_FP16X3, "bf16": TC_BF16X1}
+
+    def __init__(self, bits: int, n_fft: int, precision="bf16x3", window="rect", device: int = 0):
+        prec = self.PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+        taps = None
+        if isinstance(window, str):
+            win = {"rect": WIN_RECT, "hann": WIN_HANN}[window]
+        else:
+            self._taps = np.ascontiguousarray(window, dtype=np.float32)
+            win, taps = WIN_CUSTOM, self._taps.ctypes.data_as(ctypes.c_void_p)
+        h = ctypes.c_void_p()
+        rc = load().polaris_tc_create(int(n_fft), int(bits), win, taps, prec, int(device), ctypes.byref(h))
+        if rc != OK:
+            raise PolarisError(rc, load().polaris_tc_last_error(None).decode())
+        self._h, self.bits, self.n_fft, self.device = h, bits, n_fft, device
+        self.n_bins = n_fft // 2 + 1
+
+    def _check(self, rc):
+        if rc != OK:
+            raise PolarisError(rc, load().polaris_tc_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().polaris_tc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_wait_limit(self, limit: int) -> None:
+        self._check(load().polaris_tc_set_wait_limit(self._h, int(limit)))
+
+    def feed(self, packed, n_samples: int, stream=None) -> None:
+        arr = (ctypes.c_void_p * 2)(*[_ptr(p) for p in packed])
+        self._check(load().polaris_tc_feed(self._h, arr, int(n_samples), _stream_ptr(stream)))
+
+    def integrate(self, stream=None):
+        """dict(autos [2, nb], cross [nb] complex128, stokes [4, nb], n_segments) on the host."""
+        import torch
+
+        nb = self.n_bins
+        dev = torch.device("cuda", self.device)
+        autos = torch.empty((2, nb), dtype=torch.float64, device=dev)
+        cross = torch.empty((nb, 2), dtype=torch.float64, device=dev)
+        stokes = torch.empty((4, nb), dtype=torch.float64, device=dev)
+        nseg = ctypes.c_int64()
+        self._check(load().polaris_tc_integrate(self._h, _ptr(autos), _ptr(cross), _ptr(stokes), ctypes.byref(nseg),
+                                                _stream_ptr(stream)))
+        c = cross.cpu().numpy()
+        return {"autos": autos.cpu().numpy(), "cross": c[:, 0] + 1j * c[:, 1], "stokes": stokes.cpu().numpy(),
+                "n_segments": nseg.value}

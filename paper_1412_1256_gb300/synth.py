@@ -26,6 +26,10 @@ Workload recipes (the paper's observations are not available; these stand in):
     (FWHM 200 channels, peak 3x the continuum, at channel 3000) with fractional
     Stokes q = 0.3, u = -0.2, v = 0.1 (in the circular basis <|R|^2> ~ I + V,
     <|L|^2> ~ I - V, <R conj L> ~ Q + iU).
+  * ``config_precision``: 2 IFs (X, Y), int8, 262144-point segments (10 s at 16 Msps =
+    610 segments); unit continuum plus a Gaussian line 40 dB above it (peak 10^4, FWHM
+    20 channels, at channel 40000) whose circular polarisation follows the Zeeman-like
+    antisymmetric profile V = 1e-3 dI/dnu (one channel as the frequency unit, Eq. 1).
 """
 from __future__ import annotations
 
@@ -34,7 +38,7 @@ import numpy as np
 __all__ = [
     "samples_per_word", "pack", "unpack_codes", "quantize", "quantize_2bit", "quantize_int8",
     "quantize_1bit", "quantize_4bit", "config_tiny", "config_paper", "paper_block", "random_codes",
-    "config_circular",
+    "config_circular", "config_precision",
 ]
 
 
@@ -220,3 +224,41 @@ def config_circular(seed: int = 1412, n_fft: int = 16384, n_segments: int = 256,
     packed = [pack(quantize_int8(x * scale), 8) for x in (xr, xl)]
     return packed, dict(bits=8, n_fft=n_fft, n_samples=n_segments * n_fft, q=q, u=u, v=v, center=center,
                         fwhm=fwhm, line_peak=line_peak, window="hann")
+
+
+def config_precision(seed: int = 1256, n_fft: int = 262144, n_segments: int = 610, line_db: float = 40.0,
+                     fwhm: float = 20.0, center: float = 40000.0, v_scale: float = 1e-3, sigma: float = 20.0):
+    """Two linear-feed IFs (X, Y) as packed int8 streams: unit continuum plus a strong
+    Gaussian line (peak 10^(line_db/10) times the continuum) whose Stokes V is
+    v_scale * dI/dnu (a Zeeman-like antisymmetric profile, one channel as the unit), made
+    per segment in the frequency domain (generator only): the line's X and Y parts are
+    X = S1, Y = -i v S1 + sqrt(1 - v^2) S2 with v = V / I_line per channel, so that
+    <|X|^2> = <|Y|^2> = I_line and <X conj Y> = i v I_line.
+    Returns (list of 2 packed uint32 arrays, dict of parameters)."""
+    rng = np.random.default_rng(seed)
+    nb = n_fft // 2 + 1
+    k = np.arange(nb, dtype=np.float64)
+    sd = fwhm / (2.0 * np.sqrt(2.0 * np.log(2.0)))
+    prof = 10.0 ** (line_db / 10.0) * np.exp(-0.5 * ((k - center) / sd) ** 2)
+    v = -v_scale * (k - center) / sd ** 2          # V / I_line of the derivative profile
+    v = np.clip(v, -1.0, 1.0)
+    c = np.sqrt(1.0 - v * v)
+
+    def cg(scale):
+        return (rng.standard_normal(nb) + 1j * rng.standard_normal(nb)) * np.sqrt(scale / 2.0)
+
+    xs, ys = [], []
+    for _ in range(n_segments):
+        s1, s2 = cg(prof), cg(prof)
+        fx = cg(1.0) + s1
+        fy = cg(1.0) - 1j * v * s1 + c * s2
+        for f in (fx, fy):
+            f[0] = f[0].real
+            f[-1] = f[-1].real
+        xs.append(np.fft.irfft(fx, n_fft))
+        ys.append(np.fft.irfft(fy, n_fft))
+    xr, yr = np.concatenate(xs), np.concatenate(ys)
+    scale = sigma / np.sqrt(0.5 * (xr.var() + yr.var()))
+    packed = [pack(quantize_int8(x * scale), 8) for x in (xr, yr)]
+    return packed, dict(bits=8, n_fft=n_fft, n_samples=n_segments * n_fft, center=center, fwhm=fwhm,
+                        line_db=line_db, v_scale=v_scale, window="hann")
