@@ -713,7 +713,7 @@ def main():
     ap.add_argument("--unique", type=int, default=2, help="distinct generated seconds (tiled over the ring)")
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--cpu-segs", type=int, default=61)
-    ap.add_argument("--cpu-repeats", type=int, default=2)
+    ap.add_argument("--cpu-repeats", type=int, default=6)
     ap.add_argument("--batch-segments", type=int, default=0,
                     help="segments per kernel pass (0: the library's default, sized to keep the slab in L2)")
     ap.add_argument("--no-e2e", action="store_true")
