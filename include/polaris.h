@@ -136,6 +136,16 @@ int spectrometer_feed(polaris_spec* s, const void* const* packed, int64_t n_samp
 int spectrometer_integrate(polaris_spec* s, const polaris_stokes_params* params, float* autos, float* cross,
                            float* stokes, int64_t* n_segments_out);
 
+/* As spectrometer_integrate, but asynchronous: the readout and the copies into the
+ * caller's HOST buffers (pinned memory, for the copies to be asynchronous) are queued on
+ * cuda_stream and the call returns without synchronising.  The outputs are valid once the
+ * stream has passed this point (cudaStreamSynchronize, or an event recorded after the
+ * call).  The results are staged in the handle's device output buffers, so successive
+ * calls on one handle must be ordered (one stream).  A device-side wait that ran out
+ * shows as NaN outputs; spectrometer_integrate (synchronous) reports POLARIS_ETIMEOUT. */
+int spectrometer_integrate_async(polaris_spec* s, const polaris_stokes_params* params, float* autos, float* cross,
+                                 float* stokes, int64_t* n_segments_out, void* cuda_stream);
+
 /* As spectrometer_integrate, but the outputs are DEVICE buffers of the same
  * layouts, written in stream order on cuda_stream (no host synchronisation). */
 int spectrometer_integrate_device(polaris_spec* s, const polaris_stokes_params* params, float* d_autos, float* d_cross,

@@ -805,6 +805,26 @@ extern "C" int spectrometer_integrate_device(polaris_spec* s, const polaris_stok
   return POLARIS_OK;
 }
 
+extern "C" int spectrometer_integrate_async(polaris_spec* s, const polaris_stokes_params* prm, float* autos,
+                                            float* cross, float* stokes, int64_t* n_segments_out, void* cuda_stream) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (s->seg_acc == 0) return set_err(s, POLARIS_ESTATE, "no segment accumulated since the last integrate");
+  DeviceGuard dg(s->device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  rc = spectrometer_integrate_device(s, prm, s->d_out_autos, s->n_pair ? s->d_out_cross : nullptr,
+                                     s->n_pair ? s->d_out_stokes : nullptr, n_segments_out, cuda_stream);
+  if (rc) return rc;
+  if (autos)
+    CUDA_OR_FAIL(s, cudaMemcpyAsync(autos, s->d_out_autos, (size_t)s->nbin * 4 * s->n_if, cudaMemcpyDeviceToHost, st));
+  if (cross && s->n_pair)
+    CUDA_OR_FAIL(s, cudaMemcpyAsync(cross, s->d_out_cross, (size_t)s->nbin * 8 * s->n_pair, cudaMemcpyDeviceToHost, st));
+  if (stokes && s->n_pair)
+    CUDA_OR_FAIL(s, cudaMemcpyAsync(stokes, s->d_out_stokes, (size_t)s->nbin * 16 * s->n_pair, cudaMemcpyDeviceToHost,
+                                    st));
+  return POLARIS_OK;
+}
+
 extern "C" int spectrometer_integrate(polaris_spec* s, const polaris_stokes_params* prm, float* autos, float* cross,
                                       float* stokes, int64_t* n_segments_out) {
   int rc = check_usable(s);

@@ -985,35 +985,74 @@ static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st, bool pdl) 
     per_sm = ctas_per_sm(k_phase1<LOGN, BITS>, PL::THREADS, PL::template Stage1<BITS>::SMEM, PL::TCOLS1);
     attr_dev = dev;
   }
-  alignas(64) CUtensorMap map;
-  memset(&map, 0, sizeof map);
   using ST = typename PL::template Stage1<BITS>;
-  if constexpr (ST::STAGED && PL::N1 <= 256) {  // the kernel's TMA output path
-    if ((reinterpret_cast<uintptr_t>(a.scratch) & 15) != 0) return cudaErrorMisalignedAddress;
-    const cudaError_t e = encode_slab_map(&map, a.scratch, (long long)a.nseg * a.n_fpair * PL::N1, PL::N2, PL::CW, PL::N1);
-    if (e != cudaSuccess) return e;
-  }
-  // input maps for TMA staging (else the kernel stages with cp.async)
-  static thread_local InMaps in_maps;  // 2 KB: kept off the stack; filled, then copied by the launch
-  in_maps.use = 0;
-  constexpr int WPR_T = ST::STAGED ? ST::WPR : 1;
-  if constexpr (ST::STAGED && ST::NB == 2 && (WPR_T * 4) % 16 == 0 && PL::N1 <= 256) {
-    const long long row_bytes = (long long)PL::N2 * BITS / 8, seg_bytes = a.in.hop_w * 4;
-    bool ok = row_bytes % 16 == 0 && seg_bytes % 16 == 0;
-    const int seg_end = a.seg0 + a.nseg;  // segments [0, seg_end) of the feed are addressable
-    for (int f = 0; f < a.n_fpair && ok; ++f)
-      for (int k = 0; k < 2 && ok; ++k) {
-        const int ifx = k == 0 ? a.fa[f] : a.fb[f];
-        if (ifx < 0) continue;
-        for (int src = 0; src < 2 && ok; ++src) {
-          const long long nseg_src = src == 0 ? a.in.n0 : (long long)seg_end - a.in.n0;
-          if (nseg_src <= 0) continue;
-          const uint32_t* base = src == 0 ? a.in.src0[ifx] : a.in.src1[ifx];
-          ok = encode_input_map(&in_maps.m[src][ifx], base, PL::N2 * BITS / 32, PL::N1, nseg_src, row_bytes,
-                                seg_bytes, WPR_T) == cudaSuccess;
+  // The tensor maps (slab output, packed input) depend only on the pointers and sizes below;
+  // the last four sets per instance are kept, so that steady streaming (one or a few
+  // handles feeding equal chunks) encodes none of them again.
+  struct MapKey {
+    const void* scratch;
+    long long slab_rows, hop_w;
+    const void* base[2][kMaxIF];
+    long long nsrc[2][kMaxIF];
+  };
+  struct MapSet {
+    MapKey key;
+    alignas(64) CUtensorMap slab;
+    InMaps in;
+    bool valid;
+  };
+  static thread_local MapSet cache[4];
+  static thread_local int cache_next = 0;
+  MapKey key;
+  memset(&key, 0, sizeof key);
+  key.scratch = a.scratch;
+  key.slab_rows = (long long)a.nseg * a.n_fpair * PL::N1;
+  key.hop_w = a.in.hop_w;
+  const int seg_end = a.seg0 + a.nseg;  // segments [0, seg_end) of the feed are addressable
+  for (int f = 0; f < a.n_fpair; ++f)
+    for (int k = 0; k < 2; ++k) {
+      const int ifx = k == 0 ? a.fa[f] : a.fb[f];
+      if (ifx < 0) continue;
+      key.base[0][ifx] = a.in.src0[ifx];
+      key.base[1][ifx] = a.in.src1[ifx];
+      key.nsrc[0][ifx] = a.in.n0;
+      key.nsrc[1][ifx] = (long long)seg_end - a.in.n0;
+    }
+  MapSet* ms = nullptr;
+  for (auto& c : cache)
+    if (c.valid && memcmp(&c.key, &key, sizeof key) == 0) ms = &c;
+  if (!ms) {
+    ms = &cache[cache_next];
+    cache_next = (cache_next + 1) % 4;
+    ms->valid = false;
+    memset(&ms->slab, 0, sizeof ms->slab);
+    if constexpr (ST::STAGED && PL::N1 <= 256) {  // the kernel's TMA output path
+      if ((reinterpret_cast<uintptr_t>(a.scratch) & 15) != 0) return cudaErrorMisalignedAddress;
+      const cudaError_t e = encode_slab_map(&ms->slab, a.scratch, key.slab_rows, PL::N2, PL::CW, PL::N1);
+      if (e != cudaSuccess) return e;
+    }
+    // input maps for TMA staging (else the kernel stages with cp.async)
+    ms->in.use = 0;
+    constexpr int WPR_T = ST::STAGED ? ST::WPR : 1;
+    if constexpr (ST::STAGED && ST::NB == 2 && (WPR_T * 4) % 16 == 0 && PL::N1 <= 256) {
+      const long long row_bytes = (long long)PL::N2 * BITS / 8, seg_bytes = a.in.hop_w * 4;
+      bool ok = row_bytes % 16 == 0 && seg_bytes % 16 == 0;
+      for (int f = 0; f < a.n_fpair && ok; ++f)
+        for (int k = 0; k < 2 && ok; ++k) {
+          const int ifx = k == 0 ? a.fa[f] : a.fb[f];
+          if (ifx < 0) continue;
+          for (int src = 0; src < 2 && ok; ++src) {
+            const long long nseg_src = key.nsrc[src][ifx];
+            if (nseg_src <= 0) continue;
+            const uint32_t* base = src == 0 ? a.in.src0[ifx] : a.in.src1[ifx];
+            ok = encode_input_map(&ms->in.m[src][ifx], base, PL::N2 * BITS / 32, PL::N1, nseg_src, row_bytes,
+                                  seg_bytes, WPR_T) == cudaSuccess;
+          }
         }
-      }
-    in_maps.use = ok ? 1 : 0;
+      ms->in.use = ok ? 1 : 0;
+    }
+    ms->key = key;
+    ms->valid = true;
   }
   const long long cols = (long long)a.nseg * a.n_fpair * PL::N2;
   // staged: one unit (a tile, or half of one in the last round) per CTA pass
@@ -1030,7 +1069,7 @@ static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st, bool pdl) 
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, k_phase1<LOGN, BITS>, a, map, in_maps);
+  return cudaLaunchKernelEx(&cfg, k_phase1<LOGN, BITS>, a, ms->slab, ms->in);
 }
 
 // phase 1 of one batch

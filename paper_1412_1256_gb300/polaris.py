@@ -30,6 +30,7 @@ EXPORTS = (
     "spectrometer_last_error", "polaris_set_alloc_limit", "spectrometer_kernel_launches",
     "spectrometer_set_profiling", "spectrometer_kernel_times", "spectrometer_run_noalloc",
     "spectrometer_code_histogram", "polaris_power_from_histogram", "polaris_set_wait_limit",
+    "spectrometer_integrate_async",
     "polaris_adj_create", "polaris_adj_run", "polaris_adj_destroy", "polaris_adj_last_error",
     "polaris_tc_create", "polaris_tc_feed", "polaris_tc_integrate", "polaris_tc_set_wait_limit",
     "polaris_tc_destroy", "polaris_tc_last_error",
@@ -78,6 +79,9 @@ def load(path: str = LIB_PATH):
             lib.spectrometer_integrate_device.argtypes = [vp, ctypes.POINTER(polaris_stokes_params), vp, vp, vp,
                                                           ctypes.POINTER(i64), vp]
             lib.spectrometer_integrate_device.restype = ci
+            lib.spectrometer_integrate_async.argtypes = [vp, ctypes.POINTER(polaris_stokes_params), vp, vp, vp,
+                                                         ctypes.POINTER(i64), vp]
+            lib.spectrometer_integrate_async.restype = ci
             lib.spectrometer_n_bins.argtypes = [vp]
             lib.spectrometer_n_bins.restype = i64
             lib.spectrometer_n_pairs.argtypes = [vp]
@@ -288,6 +292,19 @@ class Spectrometer:
         self._check(load().spectrometer_integrate_device(
             self._h, ctypes.byref(p), None if autos is None else _ptr(autos), None if cross is None else _ptr(cross),
             None if stokes is None else _ptr(stokes), ctypes.byref(nseg), _stream_ptr(stream)))
+        del g
+        return int(nseg.value)
+
+    def integrate_async(self, out, feed: int = FEED_LINEAR, psi: float = 0.0, gains=None, stream=None) -> int:
+        """Queue the readout and the copies into the HOST arrays of `out` ('autos' [n_if, nb],
+        'cross' [n_pair, nb, 2], 'stokes' [n_pair, 4, nb], float32, C-contiguous; pinned for
+        asynchronous copies; missing keys skip) on `stream` without waiting.  The arrays
+        are valid once the stream has passed this call.  Returns the segment count."""
+        nseg = ctypes.c_int64(0)
+        p, g = self._params(feed, psi, gains)
+        ptr = [None if out.get(k) is None else _ptr(out[k]) for k in ("autos", "cross", "stokes")]
+        self._check(load().spectrometer_integrate_async(self._h, ctypes.byref(p), ptr[0], ptr[1], ptr[2],
+                                                        ctypes.byref(nseg), _stream_ptr(stream)))
         del g
         return int(nseg.value)
 
