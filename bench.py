@@ -535,7 +535,9 @@ def run_ours(args, rank, world, local_rank, dist):
 
     # e2e through the C ABI with pinned host buffers: every step copies its input from
     # pinned host memory (feed with host pointers) and reads its spectra back into pinned
-    # host memory (integrate_async: readout and copies queued in one call).  Two spectrometer handles on two streams take alternate steps, so that
+    # host memory (integrate_async: readout and copies queued in one call).  The feed returns
+    # once its input is read (host_async measured slower here: the host then runs far enough
+    # ahead for the two handles' kernels to overlap and compete for the SMs).  Two spectrometer handles on two streams take alternate steps, so that
     # step i+1's host-to-device copy overlaps step i's kernels (a streaming caller's
     # pattern); the host waits for step i's outputs only after queueing step i+1.
     e2e_value = None

@@ -113,14 +113,20 @@ int spectrometer_create(const polaris_config* cfg, polaris_spec** out);
 
 /* Feed n_samples_per_if new samples of every IF stream and accumulate all whole
  * segments they complete into the current integration.
- *   packed[i]   pointer to IF i's words (n_samples_per_if * bits / 32 words);
- *               host memory when on_device == 0, device memory otherwise.  Must
- *               be 4-byte aligned.
+ *   packed[i]   pointer to IF i's words (n_samples_per_if * bits / 32 words), 4-byte
+ *               aligned, in the memory that on_device names:
+ *   on_device   POLARIS_INPUT_HOST (0): host memory, read when the call returns;
+ *               POLARIS_INPUT_DEVICE (1): device memory, read in stream order (keep it
+ *               alive until the stream reaches this point);
+ *               POLARIS_INPUT_HOST_ASYNC (2): host memory (pinned, for the copy to be
+ *               asynchronous), copied in stream order: the call returns at once and the
+ *               buffers must stay unchanged until the stream reaches this point.
  *   n_samples_per_if  >= 0, a multiple of 32/bits.
- *   cuda_stream cudaStream_t to order the work on (NULL = legacy default stream).
- * Host input has been read when the call returns.  Device input is read in
- * stream order: keep it alive until the stream reaches this point.  Work is
- * asynchronous with respect to the host for device input. */
+ *   cuda_stream cudaStream_t to order the work on (NULL = legacy default stream); feeds
+ *               and integrations of one handle go on one stream.
+ * IF streams that are rows of one host array (a constant stride) go over in one copy.
+ * Work is asynchronous with respect to the host except for the wait of mode 0. */
+enum { POLARIS_INPUT_HOST = 0, POLARIS_INPUT_DEVICE = 1, POLARIS_INPUT_HOST_ASYNC = 2 };
 int spectrometer_feed(polaris_spec* s, const void* const* packed, int64_t n_samples_per_if, int on_device,
                       void* cuda_stream);
 

@@ -609,12 +609,15 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
     if (!packed[i]) return set_err(s, POLARIS_EINVAL, "packed[%d] is NULL", i);
     if (reinterpret_cast<uintptr_t>(packed[i]) & 3) return set_err(s, POLARIS_EINVAL, "packed[%d] is not 4-byte aligned", i);
   }
+  if (on_device != POLARIS_INPUT_HOST && on_device != POLARIS_INPUT_DEVICE && on_device != POLARIS_INPUT_HOST_ASYNC)
+    return set_err(s, POLARIS_EINVAL, "on_device must be POLARIS_INPUT_HOST, _DEVICE or _HOST_ASYNC");
   if (n == 0) return POLARIS_OK;
+  const bool host_in = on_device != POLARIS_INPUT_DEVICE;
   DeviceGuard dg(s->device);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
   const int64_t nw = n / s->spw;
   const uint32_t* src[kMaxIF] = {nullptr};
-  if (!on_device) {
+  if (host_in) {
     if (nw > s->in_words_cap) {
       CUDA_OR_FAIL(s, cudaStreamSynchronize(st));
       cudaFree(s->d_in);
@@ -627,11 +630,32 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
       }
       s->in_words_cap = nw;
     }
-    for (int i = 0; i < s->n_if; ++i) {
-      CUDA_OR_FAIL(s, cudaMemcpyAsync(s->d_in + (size_t)i * s->in_words_cap, packed[i], (size_t)nw * 4,
-                                      cudaMemcpyHostToDevice, st));
-      src[i] = s->d_in + (size_t)i * s->in_words_cap;
+    // IF streams at one constant stride (rows of one host array, say) go over in one
+    // pitched copy: one API call instead of one per IF (each costs host time).  The driver
+    // refuses (at the call, queueing nothing) a pitched copy whose rows lie in different
+    // pinned allocations; then the streams go one by one.
+    const long long stride = s->n_if > 1 ? (long long)((const char*)packed[1] - (const char*)packed[0]) : 0;
+    bool uniform = s->n_if > 1 && stride >= nw * 4;
+    for (int i = 2; i < s->n_if && uniform; ++i)
+      uniform = (long long)((const char*)packed[i] - (const char*)packed[i - 1]) == stride;
+    if (uniform) {
+      // contiguous on both sides (no gap between rows): one linear copy, the cheapest call
+      const bool linear = stride == nw * 4 && s->in_words_cap == nw;
+      const cudaError_t ec =
+          linear ? cudaMemcpyAsync(s->d_in, packed[0], (size_t)nw * 4 * s->n_if, cudaMemcpyHostToDevice, st)
+                 : cudaMemcpy2DAsync(s->d_in, (size_t)s->in_words_cap * 4, packed[0], (size_t)stride, (size_t)nw * 4,
+                                     (size_t)s->n_if, cudaMemcpyHostToDevice, st);
+      if (ec != cudaSuccess) {
+        cudaGetLastError();
+        uniform = false;
+      }
     }
+    if (!uniform) {
+      for (int i = 0; i < s->n_if; ++i)
+        CUDA_OR_FAIL(s, cudaMemcpyAsync(s->d_in + (size_t)i * s->in_words_cap, packed[i], (size_t)nw * 4,
+                                        cudaMemcpyHostToDevice, st));
+    }
+    for (int i = 0; i < s->n_if; ++i) src[i] = s->d_in + (size_t)i * s->in_words_cap;
     CUDA_OR_FAIL(s, cudaEventRecord(s->ev_h2d, st));
   } else {
     for (int i = 0; i < s->n_if; ++i) src[i] = static_cast<const uint32_t*>(packed[i]);
@@ -738,7 +762,7 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
   s->carry_sel ^= 1;
   s->carry_len = keep;
   s->seg_acc += nseg;
-  if (!on_device) CUDA_OR_FAIL(s, cudaEventSynchronize(s->ev_h2d));  // host input has been read
+  if (on_device == POLARIS_INPUT_HOST) CUDA_OR_FAIL(s, cudaEventSynchronize(s->ev_h2d));  // host input has been read
   return POLARIS_OK;
 }
 

@@ -22,6 +22,7 @@ OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT = 0, -1, -2, -3, -4, -5
 WIN_RECT, WIN_HANN, WIN_CUSTOM = 0, 1, 2
 FEED_LINEAR, FEED_CIRCULAR = 0, 1
 TC_BF16X3, TC_FP16X3, TC_BF16X1 = 0, 1, 2
+INPUT_HOST, INPUT_DEVICE, INPUT_HOST_ASYNC = 0, 1, 2
 STATUS_NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ESTATE: "ESTATE", ETIMEOUT: "ETIMEOUT"}
 
 EXPORTS = (
@@ -229,16 +230,18 @@ class Spectrometer:
     def __exit__(self, *a):
         self.close()
 
-    def feed(self, packed, n_samples: int, on_device: bool | None = None, stream=None) -> None:
-        """packed: one array/tensor of uint32 words per IF (numpy -> host, torch CUDA -> device)."""
+    def feed(self, packed, n_samples: int, on_device: bool | None = None, stream=None, host_async: bool = False) -> None:
+        """packed: one array/tensor of uint32 words per IF (numpy -> host, torch CUDA -> device).
+        host_async (host input only): queue the copy and return at once; the host arrays
+        (pinned, for an asynchronous copy) must stay unchanged until the stream passes."""
         if on_device is None:
             on_device = not isinstance(packed[0], np.ndarray)
         if not on_device:
             packed = [np.ascontiguousarray(p, dtype=np.uint32) for p in packed]
         arr = (ctypes.c_void_p * self.n_if)(*[_ptr(p) for p in packed])
         self._keep = packed
-        self._check(load().spectrometer_feed(self._h, arr, int(n_samples), int(bool(on_device)),
-                                             _stream_ptr(stream)))
+        mode = INPUT_DEVICE if on_device else (INPUT_HOST_ASYNC if host_async else INPUT_HOST)
+        self._check(load().spectrometer_feed(self._h, arr, int(n_samples), mode, _stream_ptr(stream)))
 
     @staticmethod
     def _params(feed: int, psi: float, gains):

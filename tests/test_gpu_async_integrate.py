@@ -44,7 +44,7 @@ def test_async_integrate_two_handles_alternating(env, orc):
             host = [t.numpy().view(np.uint32) for t in pinned]
             sp, st = sps[i % 2], streams[i % 2]
             out = _pinned_out(torch, n_if, len(pairs), n_fft // 2 + 1)
-            sp.feed(host, n, on_device=False, stream=st)
+            sp.feed(host, n, on_device=False, stream=st, host_async=(i % 2 == 1))
             nseg = sp.integrate_async(out, stream=st)
             assert nseg == c
             st.synchronize()
@@ -70,3 +70,37 @@ def test_async_integrate_needs_segments(env):
         with pytest.raises(pol.PolarisError) as ei:
             sp.integrate_async(_pinned_out(torch, 2, 1, 513))
         assert ei.value.code == pol.ESTATE
+
+
+@pytest.mark.parametrize("pad_words", [0, 48])
+def test_host_feed_from_rows_of_one_array(env, orc, pad_words):
+    """IF streams that are rows of one host array (constant stride, with or without padding
+    after each row) go over in one pitched copy; uneven feeds keep the carry right."""
+    torch, pol = env
+    n_if, bits, n_fft, hop = 4, 2, 4096, 2048
+    n = n_fft * 9 + 1024
+    rng = np.random.default_rng(55 + pad_words)
+    packed = [synth.pack(synth.random_codes(rng, n, bits), bits) for _ in range(n_if)]
+    words = n * bits // 32
+    big = np.zeros((n_if, words + pad_words), np.uint32)
+    for i in range(n_if):
+        big[i, :words] = packed[i]
+    with pol.Spectrometer(n_if, bits, n_fft, hop=hop) as sp:
+        pos = 0
+        for c in (4096, 20480, n - 24576):
+            sp.feed([big[i, pos // 16:(pos + c) // 16] for i in range(n_if)], c)
+            pos += c
+        got = sp.integrate()
+    ref = orc.spectrometer(packed, bits, n_fft, n, hop=hop)
+    assert_close(got, ref, [(0, 2), (1, 3)], 1e-5)
+
+
+def test_feed_mode_is_checked(env):
+    torch, pol = env
+    import ctypes
+
+    with pol.Spectrometer(2, 2, 1024) as sp:
+        words = np.zeros(64, np.uint32)
+        arr = (ctypes.c_void_p * 2)(words.ctypes.data, words.ctypes.data)
+        rc = pol.load().spectrometer_feed(sp._h, arr, 1024, 3, None)
+        assert rc == pol.EINVAL
