@@ -186,6 +186,23 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------
 # inputs
 # ------------------------------------------------------------------------------------------
+def slowest(dist, seconds: float) -> float:
+    """The largest of every rank's time (gloo all-reduce MAX; one rank: itself)."""
+    if dist is None:
+        return float(seconds)
+    import torch
+
+    tt = torch.tensor([float(seconds)], dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(world: int, steps: int, samples_per_step: int, seconds: float) -> float:
+    """Msample/s of all ranks together: every rank processes its own samples_per_step per
+    step (weak scaling), over the slowest rank's time."""
+    return world * steps * samples_per_step / seconds / 1e6
+
+
 def make_unique_seconds(n_unique: int):
     from paper_1412_1256_gb300 import synth
 
@@ -220,7 +237,7 @@ def run_reference(args, rank):
     unique = make_unique_seconds(1)
     # size the per-step sample so that warmup + steps take about a minute
     _, t1 = time_oracle(unique, 1)
-    budget = 60.0 / max(1, args.steps + args.warmup)
+    budget = args.ref_seconds / max(1, args.steps + args.warmup)
     segs = int(max(1, min(SEGS, budget / max(t1, 1e-3))))
     for _ in range(args.warmup):
         time_oracle(unique, segs)
@@ -517,12 +534,8 @@ def run_ours(args, rank, world, local_rank, dist):
     barrier()
     launches = sp.kernel_launches() - l0
     t_ms = e0.elapsed_time(e1)
-    t_max = t_ms
-    if dist is not None:
-        tt = torch.tensor([t_ms], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * args.steps * SAMPLES_PER_STEP / (t_max * 1e-3) / 1e6
+    t_max = slowest(dist, t_ms)
+    value = whole_job_rate(world, args.steps, SAMPLES_PER_STEP, t_max * 1e-3)
 
     # per-kernel device time: a second timed pass with every launch bracketed by events
     sp.set_profiling(True)
@@ -579,12 +592,8 @@ def run_ours(args, rank, world, local_rank, dist):
                 assert e2e_issue(i + 1) == SEGS
             e2e_wait(i)  # step i's spectra are in host memory
         torch.cuda.synchronize(dev)
-        dt = time.perf_counter() - t0
-        if dist is not None:
-            tt = torch.tensor([dt], dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt.item())
-        e2e_value = world * e2e_steps * SAMPLES_PER_STEP / dt / 1e6
+        dt = slowest(dist, time.perf_counter() - t0)
+        e2e_value = whole_job_rate(world, e2e_steps, SAMPLES_PER_STEP, dt)
         lanes[1][0].close()
 
     # variants of the same workload (NEXT-4): 50% overlap (hop = N/2, Sec. 3.1) and the
@@ -712,6 +721,8 @@ def main():
     ap.add_argument("--unique", type=int, default=2, help="distinct generated seconds (tiled over the ring)")
     ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--cpu-segs", type=int, default=61)
+    ap.add_argument("--ref-seconds", type=float, default=60.0,
+                    help="reference arm: about this many seconds of oracle work over warmup + steps")
     ap.add_argument("--cpu-repeats", type=int, default=6)
     ap.add_argument("--batch-segments", type=int, default=0,
                     help="segments per kernel pass (0: the library's default, sized to keep the slab in L2)")
