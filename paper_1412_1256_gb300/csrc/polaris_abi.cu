@@ -85,43 +85,47 @@ struct ReadoutArgs {
   const int* err;  // nonzero: a phase kernel gave up a wait; every output is NaN
 };
 
-// Readout of one block: TD consecutive values of d times all N1 values of c, i.e. the natural
-// bins k = c + N1 d in [N1 d0, N1 (d0 + TD)).  Reads walk the native layout along d (runs of TD
-// consecutive or reversed slots per c), writes walk k; a padded shared tile turns one into the
-// other.  The map k -> native slot is a bijection, so the block also clears the slots it read:
-// the accumulators start the next integration at zero without a separate memset.
-constexpr int kReadoutMinTile = 512;  // natural bins per block (at least N1; TD >= 2 at N1 <= 256)
+// Readout of one block: a tile of CT consecutive columns c times DT consecutive values of d,
+// i.e. the natural bins k = c + N1 d of those (c, d).  Reads walk the native layout along d
+// (runs of DT consecutive or reversed slots per c: 256 contiguous bytes), writes walk k (CT
+// consecutive bins per d: 128-byte lines per output array); a padded shared tile turns one
+// into the other.  The map k -> native slot is a bijection, so the block also clears the
+// slots it read: the accumulators start the next integration at zero without a memset.
+constexpr int kReadoutTile = 512;  // bins per block
 constexpr int kReadoutThreads = 256;
+constexpr int readout_ct(int n1) { return n1 < 32 ? n1 : 32; }
 
 template <int LN1>
 __global__ void __launch_bounds__(kReadoutThreads) k_readout(ReadoutArgs a) {
   constexpr int N1 = 1 << LN1;
-  constexpr int TD = N1 >= kReadoutMinTile ? 1 : kReadoutMinTile / N1, TE = TD * N1;
-  constexpr int PT = (TE + kReadoutThreads - 1) / kReadoutThreads;  // entries per thread
-  __shared__ float4 tile[TD * (N1 + 1)];
+  constexpr int CT = readout_ct(N1), DT = kReadoutTile / CT;
+  constexpr int PT = kReadoutTile / kReadoutThreads;  // entries per thread
+  __shared__ float4 tile[DT * (CT + 1)];
   asm volatile("griddepcontrol.wait;\n" ::: "memory");  // accumulators complete (dependent launch)
   // the next feed's phase 1 may set up alongside (it waits for this grid before touching data)
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   const int f = blockIdx.y, N2 = a.N2;
-  const int d0 = blockIdx.x * TD;
+  constexpr int CB = N1 / CT;  // column blocks
+  const int c0 = (blockIdx.x % CB) * CT, d0 = (blockIdx.x / CB) * DT;
   const size_t fo = (size_t)f * a.native;
   int slot[PT], sidx[PT];
   float4 v[PT];
-  // all loads first (several in flight per thread), then the clears and the shared stores
+  // all loads first (several in flight per thread), then the clears and the shared stores;
+  // consecutive threads take consecutive d of one column
 #pragma unroll
   for (int i = 0; i < PT; ++i) {
     const int e = threadIdx.x + i * kReadoutThreads;
     slot[i] = -1;
-    const int c = e / TD, dd = e % TD, d = d0 + dd;
+    const int dd = e % DT, cc = e / DT, c = c0 + cc, d = d0 + dd;
     const int k = c + N1 * d;
-    if (e >= TE || k >= a.nbin) continue;
+    if (k >= a.nbin) continue;
     int idx;
     if (c == 0) idx = d;
     else if (c == N1 / 2) idx = (d <= N2 / 2 - 2) ? N2 / 2 + 1 + d : a.UPS * N2;
     else if (c < N1 / 2) idx = c * N2 + d;
     else idx = (N1 - c) * N2 + (N2 - 1 - d);
     slot[i] = idx;
-    sidx[i] = dd * (N1 + 1) + c;
+    sidx[i] = dd * (CT + 1) + cc;
     if (a.fp64) {
       const double4 w = reinterpret_cast<const double4*>(a.acc)[fo + idx];
       v[i] = make_float4((float)(0.25 * w.x), (float)(0.25 * w.y), (float)(0.25 * w.z), (float)(0.25 * w.w));
@@ -152,11 +156,12 @@ __global__ void __launch_bounds__(kReadoutThreads) k_readout(ReadoutArgs a) {
     ig_re = a.ig_re[p];
     ig_im = a.ig_im[p];
   }
-  for (int e = threadIdx.x; e < TE; e += kReadoutThreads) {
-    const int k = N1 * d0 + e;
-    if (k >= a.nbin) break;
-    const int dd = e / N1, c = e - dd * N1;
-    float4 v = tile[dd * (N1 + 1) + c];
+  // consecutive threads take consecutive c of one d (consecutive bins)
+  for (int e = threadIdx.x; e < kReadoutTile; e += kReadoutThreads) {
+    const int cc = e % CT, dd = e / CT;
+    const int k = c0 + cc + N1 * (d0 + dd);
+    if (k >= a.nbin) continue;
+    float4 v = tile[dd * (CT + 1) + cc];
     if (failed) {
       const float qnan = __int_as_float(0x7fc00000);
       v = make_float4(qnan, qnan, qnan, qnan);
@@ -190,8 +195,8 @@ __global__ void __launch_bounds__(kReadoutThreads) k_readout(ReadoutArgs a) {
 }
 
 static dim3 readout_grid(int N1, int N2, int n_fpair) {
-  const int td = N1 >= kReadoutMinTile ? 1 : kReadoutMinTile / N1;
-  return dim3((unsigned)((N2 / 2 + 1 + td - 1) / td), (unsigned)n_fpair);
+  const int ct = readout_ct(N1), dt = kReadoutTile / ct;
+  return dim3((unsigned)((N1 / ct) * ((N2 / 2 + 1 + dt - 1) / dt)), (unsigned)n_fpair);
 }
 
 static cudaError_t launch_readout(const ReadoutArgs& r, int n_fpair, cudaStream_t st, bool pdl) {
