@@ -528,13 +528,14 @@ extern "C" int spectrometer_create(const polaris_config* cfg, polaris_spec** out
     delete s;
     return set_err(nullptr, POLARIS_ENOMEM, "cudaMalloc failed");
   }
-  // twiddles W_N^{b u} for b < N2, u <= N1/2, in FP64 then rounded
+  // twiddles W_N^{b u} for b < N2, u <= N1/2, in FP64 then rounded; unit-major ([u][b]), so
+  // that the lanes of a phase-2 item (consecutive b of one unit) read one contiguous run
   std::vector<float2> tw((size_t)s->N2 * (s->UPS + 1));
   for (int b = 0; b < s->N2; ++b)
     for (int u = 0; u <= s->UPS; ++u) {
       const int64_t e = ((int64_t)b * u) % N;
       const double ang = -2.0 * M_PI * (double)e / (double)N;
-      tw[(size_t)b * (s->UPS + 1) + u] = make_float2((float)std::cos(ang), (float)std::sin(ang));
+      tw[(size_t)u * s->N2 + b] = make_float2((float)std::cos(ang), (float)std::sin(ang));
     }
   cudaError_t e = cudaMemcpy(s->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice);
   if (e == cudaSuccess && c.window != POLARIS_WIN_RECT) {
@@ -978,12 +979,12 @@ static const int kNoallocMaxDevices = 64;
 static void* g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
 static std::mutex g_noalloc_mu;
 
-// twiddles W_N^{b u} (b < N2, u <= N1/2) in FP64, rounded once to f32
+// twiddles W_N^{b u} (b < N2, u <= N1/2) in FP64, rounded once to f32, unit-major ([u][b])
 __global__ void k_noalloc_twiddles(float2* tw, int N2, int UPS, long long N) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = (long long)N2 * (UPS + 1);
   if (i >= total) return;
-  const long long b = i / (UPS + 1), u = i % (UPS + 1);
+  const long long u = i / N2, b = i % N2;
   const long long e = (b * u) % N;
   double s, c;
   sincospi(-2.0 * (double)e / (double)N, &s, &c);

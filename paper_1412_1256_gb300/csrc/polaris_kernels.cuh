@@ -68,7 +68,7 @@ struct BatchArgs {
   int nseg;             // segments in this batch
   const float* taps;    // window taps (N) or nullptr for the rectangular window
   float2* scratch;      // slab [nseg * n_fpair][N1][N2]: row c (phase-1 output index), b contiguous
-  const float2* tw;     // [N2][UPS + 1]: W_N^{b u}
+  const float2* tw;     // [UPS + 1][N2]: W_N^{b u} (unit-major)
   void* acc;            // native accumulators [n_fpair][N/2 + 1] of float4 (or double4 if fp64)
   int fp64;
   int bits;
@@ -657,8 +657,9 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
   const long long nw = (long long)gridDim.x * PL::WARPS;
   for (long long item = (long long)blockIdx.x * PL::WARPS + warp; item < n_items; item += nw) {
     const int rg = (int)(item % NRG);
-    const int fug = (int)(item / NRG);
-    const int ug = fug % UGW, f = fug / UGW;
+    const long long fug = item / NRG;
+    const int r_begin = rg * range_len, r_end = min(R, r_begin + range_len);
+    const int ug = (int)(fug % UGW), f = (int)(fug / UGW);
     const int u = (SL > 1) ? uoff : ug * UPW + uoff;
     const int c = (u == 0) ? (e1 ? N1 / 2 : 0) : (e1 ? N1 - u : u);
     const int tu = (u == 0 && e1) ? N1 / 2 : u;
@@ -679,7 +680,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
         constexpr int k = decltype(k_)::value;
         constexpr int t = 8 * cc + k;
         float2 w = make_float2(0.f, 0.f);
-        if constexpr (t < P) w = __ldg(a.tw + (size_t)(q2 + Q2 * t) * (UPS + 1) + tu);
+        if constexpr (t < P) w = __ldg(a.tw + (size_t)tu * N2 + (q2 + Q2 * t));
         w16[2 * k] = w.x;
         w16[2 * k + 1] = w.y;
       });
@@ -692,12 +693,11 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
     }
     float extra[4] = {0.f, 0.f, 0.f, 0.f};
     bool worked = false;
-    const int r_end = min(R, (rg + 1) * range_len);
     if constexpr (PF) {
-      if (rg * range_len < r_end) {
+      if (r_begin < r_end) {
         fence_async_shared();  // the previous item's shared reads of the region come first
         __syncwarp();
-        prefetch(f, u, rg * range_len);
+        prefetch(f, u, r_begin);
       }
     }
     // after the region is free: start the next segment's copy
@@ -710,7 +710,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
         }
       }
     };
-    for (int rnd = rg * range_len; rnd < r_end; ++rnd) {
+    for (int rnd = r_begin; rnd < r_end; ++rnd) {
       const int s = rnd * SL + so;
       const bool act = s < a.nseg;
       worked |= act;
@@ -1102,7 +1102,9 @@ cudaError_t run_phase2(const BatchArgs& a, cudaStream_t st, bool pdl) {
   const long long warps = (long long)per_sm * a.num_sms * PL::WARPS;
   const int R = (a.nseg + PL::SL - 1) / PL::SL;
   const long long groups = (long long)a.n_fpair * PL::UGW;
-  // as many segment ranges per (pair, unit group) as leave every warp at most one item
+  // as many segment ranges per (pair, unit group) as leave every warp at most one item; the
+  // ranges of one group go to consecutive warps (they share the group's twiddles and slab
+  // columns)
   long long nrg = warps / groups;
   if (nrg < 1) nrg = 1;
   if (nrg > R) nrg = R;
