@@ -286,23 +286,55 @@ struct Plan {
   static constexpr size_t REGIONS1 = sizeof(float2) * (size_t)WARPS * REGION1;
   template <int BITS>
   struct Stage1 {
+    static constexpr int tile_of(int ipt) { return ipt * WARPS * CW; }
+    static constexpr int wpr_of(int ipt) { return tile_of(ipt) * BITS / 32; }
     // staged row: the tile's words of the two IFs interleaved (word w of IF a, of IF b, ...)
-    // so that one 8-byte load fetches both, plus two pad words (rows of distinct q1 then fall
-    // on distinct bank pairs)
-    static constexpr int row_words(int ipt) { return 2 * (ipt * WARPS * CW * BITS / 32) + 2; }
+    // so that one 8-byte load fetches both, padded to an odd number of 8-byte pairs (rows of
+    // distinct q1 then fall on distinct bank pairs)
+    static constexpr int row_words(int ipt) { return 2 * wpr_of(ipt) + (wpr_of(ipt) % 2 ? 0 : 2); }
     static constexpr bool fits(int ipt, int bufs) {
       return REGIONS1 + 4 * (size_t)bufs * N1 * row_words(ipt) + 32 <= kSmemPerCta2;
     }
-    static constexpr bool ok(int ipt) {
-      return N2 % (ipt * WARPS * CW) == 0 && (ipt * WARPS * CW) % 32 == 0 && fits(ipt, 2);
+    // a tile of whole words that divides N2
+    static constexpr bool aligned(int ipt) {
+      return N2 % tile_of(ipt) == 0 && (tile_of(ipt) * BITS) % 32 == 0 && tile_of(ipt) * BITS >= 32;
     }
-    static constexpr int IPT = ok(2) ? 2 : 1;
+    static constexpr bool ok(int ipt) { return aligned(ipt) && tile_of(ipt) % 32 == 0 && fits(ipt, 2); }
+    // Column groups per tile, 0 = not staged.  Tiles of 32 or more columns first; for
+    // N1 >= 512 (warps of one or two columns, whose unstaged loads would each touch 32
+    // sectors) any tile of whole words, preferring two stage buffers, then more columns.
+    static constexpr int pick() {
+      return ok(2)                                                 ? 2
+             : (N2 % tile_of(1) == 0 && tile_of(1) % 32 == 0)     ? 1
+             : N1 < 512                                           ? 0
+             : (aligned(2) && fits(2, 2))                         ? 2
+             : (aligned(1) && fits(1, 2))                         ? 1
+             : (aligned(2) && fits(2, 1))                         ? 2
+             : (aligned(1) && fits(1, 1))                         ? 1
+                                                                  : 0;
+    }
+    static constexpr int IPT = pick() > 0 ? pick() : 1;
     static constexpr int TILE = IPT * WARPS * CW;
-    static constexpr bool STAGED = (N2 % TILE == 0) && (TILE % 32 == 0);
+    static constexpr bool STAGED = pick() > 0;
     static constexpr int WPR = TILE * BITS / 32;  // words per IF per staged row
     static constexpr int RS = row_words(IPT);
     static constexpr int NB = fits(IPT, 2) ? 2 : 1;  // 2: the next tile in flight
     static constexpr int WORDS = STAGED ? NB * N1 * RS : 0;
+    // TMA boxes are at most 256 rows: larger N1 moves by N1 / BOXR boxes per copy
+    static constexpr int BOXR = N1 < 256 ? N1 : 256;
+    // N1 <= 256: the warp's [N1][CW] output block leaves by one TMA store (rows of 32 bytes
+    // or more).  N1 >= 512 (warps of one or two columns): the column group's [N1][WARPS CW]
+    // block is assembled in the CTA's transpose regions, which it fits, and leaves by
+    // N1 / BOXR TMA stores of 64- or 128-byte rows (swizzled in shared memory); per-warp
+    // stores of 8- or 16-byte rows measured several times slower.
+    static constexpr int JC = WARPS * CW;  // columns of the joint block
+    static constexpr bool TMA_OUT = STAGED && Q1 > 1 && N1 <= 256;
+    static constexpr bool JOINT_OUT = STAGED && Q1 > 1 && N1 >= 512 && (JC * 8 == 64 || JC * 8 == 128) &&
+                                      (size_t)N1 * JC * 8 <= REGIONS1;
+    static constexpr int JSW = JC * 8 == 128 ? 7 : 3;  // swizzle mask: 128-byte (SW128) or 64-byte (SW64) rows
+    // the tile's input may be staged by TMA (two buffers, 16-byte box rows, one box of all
+    // N1 rows: at N1 = 512 two boxes of 256 rows measured slower than cp.async staging)
+    static constexpr bool TMA_IN = STAGED && NB == 2 && (WPR * 4) % 16 == 0 && N1 <= 256;
     static constexpr size_t SMEM = REGIONS1 + 4 * (size_t)WORDS + 16 + 16;  // + 2 mbarriers + TMEM slot
   };
 

@@ -105,6 +105,13 @@ __device__ __forceinline__ void tma_store_2d_elect(const CUtensorMap* map, const
       "r"(smem_addr(src)), "r"(x), "r"(y)
       : "memory");
 }
+// TMA store of a 2-D box by the calling thread alone (the caller commits the group)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];\n" ::"l"(map), "r"(src),
+               "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
 // wait until this thread's bulk groups have finished reading shared memory (a lane that
 // issued none returns at once)
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
@@ -276,20 +283,34 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
   using ST = typename PL::template Stage1<BITS>;
   constexpr bool STAGED = ST::STAGED;
   constexpr int TILE = ST::TILE, IPT = ST::IPT, WPR = STAGED ? ST::WPR : 1;  // words per IF per tile row
-  // the warp's [N1][CW] output block leaves by one TMA store (a box is at most 256 rows)
-  constexpr bool TMA_OUT = STAGED && N1 <= 256;
-  static_assert(!TMA_OUT || (Q1 > 1 && N1 <= 256 && N1 * CW <= PL::REGION1 && (PL::REGION1 * 8) % 128 == 0),
+  // the warp's [N1][CW] output block leaves by one TMA store (TMA_OUT), or the column
+  // group's [N1][JC] block, assembled over all warps' regions, by N1 / BOXR (JOINT)
+  constexpr bool TMA_OUT = ST::TMA_OUT, JOINT = ST::JOINT_OUT;
+  constexpr int BOXR = ST::BOXR, JC = ST::JC;
+  static_assert(!TMA_OUT || (Q1 > 1 && N1 == BOXR && (CW * 8) % 16 == 0 && N1 * CW <= PL::REGION1 &&
+                             (PL::REGION1 * 8) % 128 == 0),
                 "TMA output tile");
-  extern __shared__ __align__(128) float2 sm1[];
+  static_assert(!JOINT || (N1 % BOXR == 0 && (BOXR * JC * 8) % 1024 == 0 && (size_t)N1 * JC * 8 <= PL::REGIONS1),
+                "joint output block");
+  extern __shared__ __align__(1024) float2 sm1[];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if constexpr (JOINT) {
+    // the swizzled joint block needs a 1024-byte aligned base (the declaration asks for it);
+    // should that ever not hold, report and leave the work undone rather than misplace data
+    if ((smem_addr(sm1) & 1023u) != 0) {
+      if (tid == 0 && a.err) atomicExch(a.err, 1);
+      return;
+    }
+  }
   const int q1 = lane / CW, cw = lane % CW;
   float2* region = sm1 + warp * PL::REGION1;
   uint32_t* stage = reinterpret_cast<uint32_t*>(sm1 + PL::WARPS * PL::REGION1);  // stage buffers
   const uint32_t bar0 = smem_addr(stage + ST::WORDS);  // two mbarriers (TMA staging), then the TMEM slot
   uint32_t* tslot = stage + ST::WORDS + 4;
-  // TMA staging of the input: possible for this plan (two buffers, 16-byte box rows, boxes
-  // of at most 256 rows) and chosen by the host for this launch
-  constexpr bool TIN = STAGED && ST::NB == 2 && (WPR * 4) % 16 == 0 && N1 <= 256;
+  // TMA staging of the input: possible for this plan (two buffers, 16-byte box rows) and
+  // chosen by the host for this launch
+  constexpr bool TIN = ST::TMA_IN;
+  static_assert(!TIN || (N1 % BOXR == 0 && (BOXR * WPR * 4) % 128 == 0), "TMA input boxes");
   const bool tin = TIN && in_maps.use != 0;
   if (TIN && tin && tid == 0) {
     mbar_init(bar0, 1);
@@ -339,12 +360,50 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
         bulk_wait_read();  // the previous output tile has left the region
         __syncwarp();
       }
+      if constexpr (JOINT) {
+        if (tid == 0) bulk_wait_read();  // the previous joint block has left the regions
+        __syncthreads();
+      }
       sfor<0, P>([&](auto p_) {
         constexpr int p = decltype(p_)::value;
         region[q1 * LDQ + p * LDP + cw] = v[p];
       });
       __syncwarp();
-      if constexpr (TMA_OUT) {
+      if constexpr (JOINT) {
+        sfor<0, PQ>([&](auto r_) {
+          constexpr int r = decltype(r_)::value;
+          const int p = r * Q1 + q1;
+          sfor<0, Q1>([&](auto q_) {
+            constexpr int q = decltype(q_)::value;
+            v[r * Q1 + ct::bitrev(q, Q1)] = region[q * LDQ + p * LDP + cw];
+          });
+          dit<Q1, r * Q1, 1>(v);
+        });
+        __syncthreads();  // every warp has read its transpose: the regions take the joint block
+        // joint block [c][JC] of 8-byte values, JC * 8 = 64 or 128 bytes per row, with the
+        // TMA swizzle of that row width: 16-byte chunk k of row c sits at chunk k ^ (row
+        // bits of the byte offset), so the 16 or 32 rows one store instruction writes fall
+        // on distinct chunks
+        char* jb = reinterpret_cast<char*>(sm1);
+        sfor<0, PQ>([&](auto r_) {
+          constexpr int r = decltype(r_)::value;
+          sfor<0, Q1>([&](auto m_) {
+            constexpr int m = decltype(m_)::value;
+            uint32_t o = (uint32_t)(((r * Q1 + q1 + P * m) * JC + warp * CW + cw) * 8);
+            o ^= ((o >> 7) & (uint32_t)ST::JSW) << 4;
+            *reinterpret_cast<float2*>(jb + o) = v[r * Q1 + m];
+          });
+        });
+        fence_async_shared();
+        __syncthreads();
+        if (tid == 0 && act) {  // xcol of warp 0 = the column group's first column
+          sfor<0, N1 / BOXR>([&](auto h_) {
+            constexpr int h = decltype(h_)::value;
+            tma_store_2d(&slab_map, smem_addr(jb + h * BOXR * JC * 8), xcol, (int)(g * N1 + h * BOXR));
+          });
+          bulk_commit();
+        }
+      } else if constexpr (TMA_OUT) {
         sfor<0, PQ>([&](auto r_) {
           constexpr int r = decltype(r_)::value;
           const int p = r * Q1 + q1;
@@ -451,8 +510,9 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
       });
       cp_async_commit();
     };
-    // TMA staging: one thread loads the tile's box of each IF (N1 rows x WPR words) into a
-    // dense [IF][row][word] stage and the CTA waits on that buffer's mbarrier (bounded)
+    // TMA staging: one thread loads the tile's words of each IF (N1 rows x WPR words, in
+    // boxes of BOXR rows) into a dense [IF][row][word] stage and the CTA waits on that
+    // buffer's mbarrier (bounded)
     auto issue_tma = [&](long long tile, int buf) {
       const int g = (int)(tile / (N2 / TILE)), b0 = (int)(tile % (N2 / TILE)) * TILE;
       const int s_local = g / a.n_fpair, f = g - s_local * a.n_fpair;
@@ -460,22 +520,25 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
       const int ia = a.fa[f], ib = a.fb[f];
       const int src = sg < a.in.n0 ? 0 : 1, z = sg < a.in.n0 ? sg : sg - a.in.n0;
       const uint32_t bar = bar0 + 8u * (uint32_t)buf, dst = stage_a + 4u * (uint32_t)(buf * SB);
-      const uint32_t box = (uint32_t)(N1 * WPR * 4);
+      const uint32_t box = (uint32_t)(N1 * WPR * 4), sub = (uint32_t)(BOXR * WPR * 4);  // bytes per IF, per box
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar),
                    "r"(ib >= 0 ? 2 * box : box)
                    : "memory");
       const int x = (b0 * BITS) / 32;
-      asm volatile(
-          "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-          "[%5];\n" ::"r"(dst),
-          "l"(&in_maps.m[src][ia]), "r"(x), "r"(0), "r"(z), "r"(bar)
-          : "memory");
-      if (ib >= 0)
+      sfor<0, N1 / BOXR>([&](auto h_) {
+        constexpr int h = decltype(h_)::value;
         asm volatile(
             "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-            "[%5];\n" ::"r"(dst + box),
-            "l"(&in_maps.m[src][ib]), "r"(x), "r"(0), "r"(z), "r"(bar)
+            "[%5];\n" ::"r"(dst + h * sub),
+            "l"(&in_maps.m[src][ia]), "r"(x), "r"(h * BOXR), "r"(z), "r"(bar)
             : "memory");
+        if (ib >= 0)
+          asm volatile(
+              "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+              "[%5];\n" ::"r"(dst + box + h * sub),
+              "l"(&in_maps.m[src][ib]), "r"(x), "r"(h * BOXR), "r"(z), "r"(bar)
+              : "memory");
+      });
     };
     // Work units: whole tiles for the complete rounds over the grid, then, for the last,
     // partial round, half tiles (one column group per warp; the whole tile is staged), so
@@ -593,7 +656,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
     }
     cp_async_wait_all();
   }
-  if constexpr (TMA_OUT) {
+  if constexpr (TMA_OUT || JOINT) {
     bulk_wait_all();  // output tiles written before the CTA's shared memory goes
   }
   if constexpr (Q1 > 1) cta_tmem_end<PL::TCOLS1>(tbase, warp);
@@ -926,8 +989,10 @@ static int ctas_per_sm(K kernel, int threads, size_t smem, int tmem_cols) {
 }
 
 // Tensor map over the slab of one batch, rows (pair-segment, c) x columns b of 8-byte
-// complex values; box = one warp's output block (CW columns x N1 rows).
-static cudaError_t encode_slab_map(CUtensorMap* map, float2* slab, long long rows, int n2, int cw, int n1) {
+// complex values; box = box_cols columns x box_rows rows of an output block, laid out in
+// shared memory with the given swizzle.
+static cudaError_t encode_slab_map(CUtensorMap* map, float2* slab, long long rows, int n2, int box_cols, int box_rows,
+                                   CUtensorMapSwizzle swizzle) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
@@ -939,18 +1004,18 @@ static cudaError_t encode_slab_map(CUtensorMap* map, float2* slab, long long row
   }
   const cuuint64_t dims[2] = {(cuuint64_t)n2, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)n2 * sizeof(float2)};
-  const cuuint32_t box[2] = {(cuuint32_t)cw, (cuuint32_t)n1};
+  const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, slab, dims, strides, box, estr,
-                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
 // Tensor map over one IF's packed input: 32-bit words x rows (row_bytes apart) x segments
-// (seg_bytes apart); box = one tile's words of all rows of one segment.  Fails (and phase 1
-// then stages with cp.async) for an address that is not 16-byte aligned.
-static cudaError_t encode_input_map(CUtensorMap* map, const uint32_t* base, int words_per_row, int rows,
+// (seg_bytes apart); box = one tile's words of box_rows rows of one segment.  Fails (and
+// phase 1 then stages with cp.async) for an address that is not 16-byte aligned.
+static cudaError_t encode_input_map(CUtensorMap* map, const uint32_t* base, int words_per_row, int rows, int box_rows,
                                     long long segs, long long row_bytes, long long seg_bytes, int box_words) {
   if ((reinterpret_cast<uintptr_t>(base) & 15) != 0) return cudaErrorMisalignedAddress;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -964,7 +1029,7 @@ static cudaError_t encode_input_map(CUtensorMap* map, const uint32_t* base, int 
   }
   const cuuint64_t dims[3] = {(cuuint64_t)words_per_row, (cuuint64_t)rows, (cuuint64_t)segs};
   const cuuint64_t strides[2] = {(cuuint64_t)row_bytes, (cuuint64_t)seg_bytes};
-  const cuuint32_t box[3] = {(cuuint32_t)box_words, (cuuint32_t)rows, 1};
+  const cuuint32_t box[3] = {(cuuint32_t)box_words, (cuuint32_t)box_rows, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<uint32_t*>(base), dims, strides, box,
                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1026,15 +1091,18 @@ static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st, bool pdl) 
     cache_next = (cache_next + 1) % 4;
     ms->valid = false;
     memset(&ms->slab, 0, sizeof ms->slab);
-    if constexpr (ST::STAGED && PL::N1 <= 256) {  // the kernel's TMA output path
+    if constexpr (ST::TMA_OUT || ST::JOINT_OUT) {  // the kernel's TMA output paths
       if ((reinterpret_cast<uintptr_t>(a.scratch) & 15) != 0) return cudaErrorMisalignedAddress;
-      const cudaError_t e = encode_slab_map(&ms->slab, a.scratch, key.slab_rows, PL::N2, PL::CW, PL::N1);
+      const cudaError_t e =
+          ST::TMA_OUT ? encode_slab_map(&ms->slab, a.scratch, key.slab_rows, PL::N2, PL::CW, PL::N1,
+                                        CU_TENSOR_MAP_SWIZZLE_NONE)
+                      : encode_slab_map(&ms->slab, a.scratch, key.slab_rows, PL::N2, ST::JC, ST::BOXR,
+                                        ST::JSW == 7 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B);
       if (e != cudaSuccess) return e;
     }
     // input maps for TMA staging (else the kernel stages with cp.async)
     ms->in.use = 0;
-    constexpr int WPR_T = ST::STAGED ? ST::WPR : 1;
-    if constexpr (ST::STAGED && ST::NB == 2 && (WPR_T * 4) % 16 == 0 && PL::N1 <= 256) {
+    if constexpr (ST::TMA_IN) {
       const long long row_bytes = (long long)PL::N2 * BITS / 8, seg_bytes = a.in.hop_w * 4;
       bool ok = row_bytes % 16 == 0 && seg_bytes % 16 == 0;
       for (int f = 0; f < a.n_fpair && ok; ++f)
@@ -1045,8 +1113,8 @@ static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st, bool pdl) 
             const long long nseg_src = key.nsrc[src][ifx];
             if (nseg_src <= 0) continue;
             const uint32_t* base = src == 0 ? a.in.src0[ifx] : a.in.src1[ifx];
-            ok = encode_input_map(&ms->in.m[src][ifx], base, PL::N2 * BITS / 32, PL::N1, nseg_src, row_bytes,
-                                  seg_bytes, WPR_T) == cudaSuccess;
+            ok = encode_input_map(&ms->in.m[src][ifx], base, PL::N2 * BITS / 32, PL::N1, ST::BOXR, nseg_src,
+                                  row_bytes, seg_bytes, ST::WPR) == cudaSuccess;
           }
         }
       ms->in.use = ok ? 1 : 0;
