@@ -61,7 +61,7 @@ typedef struct polaris_spec polaris_spec; /* opaque, library-owned */
 /* Spectrometer configuration (Table 1: number of IFs, quantisation, channels).
  *   n_if        1..8 IF streams.
  *   bits        1, 2, 4 or 8 bits per sample.
- *   n_fft       segment length N, a power of two in [16, 524288]; N/2+1 bins.
+ *   n_fft       segment length N, a power of two in [16, 1048576]; N/2+1 bins.
  *   hop         segment spacing in samples, 0 < hop <= n_fft, a multiple of
  *               32/bits (0 means hop = n_fft; hop = n_fft/2 is the 50% overlap
  *               of Sec. 3.1).

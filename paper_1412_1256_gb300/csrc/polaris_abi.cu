@@ -36,6 +36,7 @@ POLARIS_DECLARE(16)
 POLARIS_DECLARE(17)
 POLARIS_DECLARE(18)
 POLARIS_DECLARE(19)
+POLARIS_DECLARE(20)
 #undef POLARIS_DECLARE
 
 // (args, stream, programmatic dependent launch on the predecessor in `stream`)
@@ -44,11 +45,11 @@ typedef cudaError_t (*phase_fn)(const BatchArgs&, cudaStream_t, bool);
 cudaError_t launch_code_hist(const SegSrc& in, int n_if, int bits, int nseg, int64_t n_fft,
                              unsigned long long* hist, int num_sms, cudaStream_t st);
 #define POLARIS_ROW(LOGN) {run_phase1<LOGN>, run_phase2<LOGN>}
-static const phase_fn kPhases[20][2] = {
+static const phase_fn kPhases[21][2] = {
     {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr},
     POLARIS_ROW(4),  POLARIS_ROW(5),  POLARIS_ROW(6),  POLARIS_ROW(7),  POLARIS_ROW(8),  POLARIS_ROW(9),
     POLARIS_ROW(10), POLARIS_ROW(11), POLARIS_ROW(12), POLARIS_ROW(13), POLARIS_ROW(14), POLARIS_ROW(15),
-    POLARIS_ROW(16), POLARIS_ROW(17), POLARIS_ROW(18), POLARIS_ROW(19)};
+    POLARIS_ROW(16), POLARIS_ROW(17), POLARIS_ROW(18), POLARIS_ROW(19), POLARIS_ROW(20)};
 #undef POLARIS_ROW
 
 // ---------------------------------------------------------------------------------------
@@ -214,7 +215,7 @@ static cudaError_t launch_readout(const ReadoutArgs& r, int n_fpair, cudaStream_
   case 1 << LN1:                                              \
     return cudaLaunchKernelEx(&cfg, k_readout<LN1>, r);
     POLARIS_RO(1) POLARIS_RO(2) POLARIS_RO(3) POLARIS_RO(4) POLARIS_RO(5) POLARIS_RO(6) POLARIS_RO(7)
-    POLARIS_RO(8) POLARIS_RO(9) POLARIS_RO(10)
+    POLARIS_RO(8) POLARIS_RO(9) POLARIS_RO(10) POLARIS_RO(11)
 #undef POLARIS_RO
     default: return cudaErrorInvalidValue;
   }
@@ -392,8 +393,8 @@ extern "C" int spectrometer_create(const polaris_config* cfg, polaris_spec** out
   if (!(c.bits == 1 || c.bits == 2 || c.bits == 4 || c.bits == 8))
     return set_err(nullptr, POLARIS_EINVAL, "bits must be 1, 2, 4 or 8");
   const int64_t N = c.n_fft;
-  if (N < 16 || N > (1 << 19) || (N & (N - 1)))
-    return set_err(nullptr, POLARIS_EINVAL, "n_fft must be a power of two in [16, 524288]");
+  if (N < 16 || N > (1 << 20) || (N & (N - 1)))
+    return set_err(nullptr, POLARIS_EINVAL, "n_fft must be a power of two in [16, 1048576]");
   const int64_t spw = 32 / c.bits;
   if (N < spw) return set_err(nullptr, POLARIS_EINVAL, "n_fft must be at least 32/bits samples");
   const int64_t hop = c.hop == 0 ? N : c.hop;
@@ -1010,8 +1011,8 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
   if (!(c.bits == 1 || c.bits == 2 || c.bits == 4 || c.bits == 8))
     return set_err(nullptr, POLARIS_EINVAL, "bits must be 1, 2, 4 or 8");
   const int64_t N = c.n_fft;
-  if (N < 16 || N > (1 << 19) || (N & (N - 1)))
-    return set_err(nullptr, POLARIS_EINVAL, "n_fft must be a power of two in [16, 524288]");
+  if (N < 16 || N > (1 << 20) || (N & (N - 1)))
+    return set_err(nullptr, POLARIS_EINVAL, "n_fft must be a power of two in [16, 1048576]");
   const int64_t spw = 32 / c.bits;
   const int64_t hop = c.hop == 0 ? N : c.hop;
   if (N < spw || hop < 1 || hop > N || hop % spw)

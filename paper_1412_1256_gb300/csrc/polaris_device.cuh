@@ -200,10 +200,11 @@ constexpr int plan_p(int logn) { return logn >= 10 ? 32 : (logn >= 8 ? 16 : (log
 // phase-1 points per lane: 16 at N1 = 128 (half the registers of 32, so three CTAs per SM,
 // with the same FFT work per point and warps still four columns = 32 bytes wide).  At
 // N1 = 256 sixteen would leave two-column warps whose 16-byte output rows split sectors;
-// that measured slower than 32 points per lane at two CTAs per SM.
-constexpr int plan_p1(int logn, int n1) { return n1 == 128 ? 16 : plan_p(logn); }
+// that measured slower than 32 points per lane at two CTAs per SM.  N1 = 2048 (N = 2^20):
+// 64 points per lane, so that one warp still holds a whole column (one CTA per SM).
+constexpr int plan_p1(int logn, int n1) { return n1 == 128 ? 16 : (n1 == 2048 ? 64 : plan_p(logn)); }
 constexpr int plan_log_n2(int logn) {
-  // 4:2 5:3 6:3 7:4 8:4 9:5 10:5 11:6 12:6 13:7 14:7 15:8 16:8 17:9 18:9 19:9
+  // 4:2 5:3 6:3 7:4 8:4 9:5 10:5 11:6 12:6 13:7 14:7 15:8 16:8 17:9 18:9 19:9 20:9
   return logn >= 17 ? 9 : (logn + 1) / 2;
 }
 // ----------------------------------------------------------------------------------------
@@ -230,6 +231,7 @@ constexpr Ld2 p1_layout(int P, int Q1) {
          : (P == 32 && Q1 == 8)  ? Ld2{4, 132}
          : (P == 32 && Q1 == 16) ? Ld2{2, 66}
          : (P == 32 && Q1 == 32) ? Ld2{1, 33}
+         : (P == 64 && Q1 == 32) ? Ld2{1, 65}
                                  : Ld2{32 / Q1, P * (32 / Q1)};  // Q1 = 1: no transpose
 }
 constexpr Ld2 p2_layout(int P, int Q2) {
@@ -275,7 +277,7 @@ struct Plan {
   static constexpr int LDP1 = L1.a, LDQ1 = L1.b;
   static constexpr int REGION1 = Q1 > 1 ? Q1 * LDQ1 : 0;  // float2 per warp
   static constexpr int TW1 = ((2 * P1 + 15) / 16) * 16;     // tensor-memory columns per lane (W_N1 twiddles)
-  static constexpr int MINB1 = P1 <= 16 ? 3 : 2;             // phase-1 CTAs per SM the registers aim at
+  static constexpr int MINB1 = P1 <= 16 ? 3 : (P1 <= 32 ? 2 : 1);  // phase-1 CTAs per SM the registers aim at
   static constexpr int TCOLS1 = pow2_at_least((WARPS / 4) * TW1, 32);
   // CTA tiles of IPT * WARPS * CW columns inside one segment (Stage1<BITS>): the CTA stages
   // the tile's packed words (both IFs) in shared memory; otherwise (small N) every lane loads
@@ -360,7 +362,7 @@ struct Plan {
 
   static_assert(N1 * N2 == N, "plan");
   static_assert(Q1 >= 1 && Q1 <= 32 && P1 % Q1 == 0 && Q2 >= 1 && 2 * Q2 <= P && 16 % Q2 == 0, "plan bounds");
-  static_assert(N1 <= 1024 && N2 <= 1024, "constant twiddle table covers L <= 1024");
+  static_assert(N1 <= 2048 && N2 <= 2048, "constant twiddle table covers L <= 2048");
   static_assert(UPS % UPW == 0 || UPW % UPS == 0, "units per warp");
   static_assert(TCOLS1 <= 256 && TCOLS2 <= 256, "tensor memory per CTA");
 };

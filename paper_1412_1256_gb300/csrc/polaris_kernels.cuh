@@ -27,25 +27,30 @@
 
 namespace polaris {
 
-// W_1024^k = e^{-2 pi i k / 1024}, k in [0, 1024), from the compile-time series.
+// W_2048^k = e^{-2 pi i k / 2048}, k in [0, 2048), from the compile-time series.  The table
+// sits in global memory (read through the read-only cache): the kernels' set-up reads a
+// different entry in every lane, which a __constant__ bank would serialise per distinct
+// address (that cost 8 us of a 45 us phase-1 launch at 2^17).
+constexpr int kTwL = 2048;
 struct TwTable {
-  float2 v[1024];
+  float2 v[kTwL];
 };
-constexpr TwTable make_tw1024() {
+constexpr TwTable make_tw_table() {
   TwTable t{};
-  for (int k = 0; k < 1024; ++k) {
-    const ct::CS cs = ct::cossin2pi(k, 1024);
+  for (int k = 0; k < kTwL; ++k) {
+    const ct::CS cs = ct::cossin2pi(k, kTwL);
     t.v[k].x = (float)cs.c;
     t.v[k].y = (float)(-cs.s);
   }
   return t;
 }
-static __constant__ TwTable c_tw = make_tw1024();
+static __device__ TwTable g_tw = make_tw_table();
 
-// twiddle W_L^k for L <= 1024 (power of two), k any integer
+// twiddle W_L^k for L <= 2048 (power of two), k any integer
 template <int L>
 __device__ __forceinline__ float2 tw_small(int k) {
-  return c_tw.v[(k & (L - 1)) * (1024 / L)];
+  static_assert(L <= kTwL && kTwL % L == 0, "twiddle table");
+  return __ldg(&g_tw.v[(k & (L - 1)) * (kTwL / L)]);
 }
 
 constexpr int kMaxIF = 8;

@@ -79,7 +79,7 @@ def test_bits(pol, orc, bits):
     assert_close(got, ref, [(0, 1)], TOL)
 
 
-@pytest.mark.parametrize("logn", [13, 14, 15, 16, 17, 18, 19])
+@pytest.mark.parametrize("logn", [13, 14, 15, 16, 17, 18, 19, 20])
 @pytest.mark.parametrize("bits", [1, 2, 4, 8])
 def test_staged_sizes_every_width(pol, orc, logn, bits):
     """Every (size, sample width) of the shared-memory-staged phase 1: tile widths, stage
@@ -178,7 +178,7 @@ def test_integrate_without_segments_is_state_error(pol):
 def test_invalid_configs(pol):
     for kw in [dict(n_if=0, bits=2, n_fft=1024), dict(n_if=2, bits=3, n_fft=1024), dict(n_if=2, bits=2, n_fft=1000),
                dict(n_if=2, bits=2, n_fft=1024, hop=8), dict(n_if=2, bits=2, n_fft=1024, pairs=[(0, 0)]),
-               dict(n_if=2, bits=1, n_fft=16)]:
+               dict(n_if=2, bits=1, n_fft=16), dict(n_if=2, bits=2, n_fft=1 << 21)]:
         with pytest.raises(pol.PolarisError) as ei:
             pol.Spectrometer(**kw)
         assert ei.value.code == pol.EINVAL
