@@ -319,7 +319,7 @@ def run_reference(args, rank):
 # ------------------------------------------------------------------------------------------
 def batch_graph_variant(torch, polaris, dev, local_rank, world, n_streams=64, seed=2024):
     """Many independent 2-IF spectrometers at once (a mixed multi-stream workload): N
-    log-uniform in 2^12..2^19, 2- or 8-bit, 0.1..2 s of 16-Msps data each (whole segments),
+    log-uniform in 2^12..2^20, 2- or 8-bit, 0.1..2 s of 16-Msps data each (whole segments),
     every handle's feed + integrate captured into one CUDA graph and replayed; reports the
     aggregate input rate, and the same work issued eagerly for comparison."""
     rng = np.random.default_rng(seed)
@@ -327,7 +327,7 @@ def batch_graph_variant(torch, polaris, dev, local_rank, world, n_streams=64, se
     items = []
     total = 0
     for _ in range(n_streams):
-        logn = int(rng.integers(12, 20))
+        logn = int(rng.integers(12, 21))
         bits = int(rng.choice([2, 8]))
         dur = float(np.exp(rng.uniform(np.log(0.1), np.log(2.0))))
         n_fft = 1 << logn
@@ -393,7 +393,7 @@ def batch_graph_variant(torch, polaris, dev, local_rank, world, n_streams=64, se
     return {"streams": n_streams, "samples_per_pass": total, "graph_ms_per_pass": graph_ms,
             "eager_ms_per_pass": eager_ms, "value": world * total / (graph_ms * 1e-3) / 1e6,
             "eager_value": world * total / (eager_ms * 1e-3) / 1e6, "unit": "Msample/s",
-            "note": "N log-uniform 2^12..2^19, 2/8-bit, 0.1..2 s at 16 Msps (whole segments), seed 2024"}
+            "note": "N log-uniform 2^12..2^20, 2/8-bit, 0.1..2 s at 16 Msps (whole segments), seed 2024"}
 
 
 def adjoint_variant(torch, polaris, dev, local_rank, world, n_ring=20, seed=1256):
