@@ -139,6 +139,15 @@ __device__ __forceinline__ void bulk_load2_elect(uint32_t bar, uint32_t dst0, co
       "r"(dst0), "l"(src0), "r"(dst1), "l"(src1), "r"(2 * bytes_each), "r"(bytes_each)
       : "memory");
 }
+// one bulk copy global -> shared completing on mbarrier `bar` (the caller has announced the bytes)
+__device__ __forceinline__ void bulk_load(uint32_t bar, uint32_t dst, const void* src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
 // true once the barrier's phase `parity` has completed; false after `limit` polls
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, uint32_t limit) {
   for (uint32_t i = 0; i < limit; ++i) {
@@ -688,7 +697,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
   float2* region = sm2 + warp * PL::REGION2;
   float2* tw2 = sm2 + PL::WARPS * PL::REGION2;  // skewed table: W_N2^k at k + k/32
   uint32_t* tslot = reinterpret_cast<uint32_t*>(tw2 + PL::TWT);
-  // prefetch (PF): the next segment's two columns arrive in the warp's region by bulk copy
+  // prefetch (PF): the next segment's columns arrive in the warp's region by bulk copy
   constexpr bool PF = PL::PF2;
   const uint32_t bar = smem_addr(reinterpret_cast<uint64_t*>(tslot + 4) + warp);
   if constexpr (PF) {
@@ -699,11 +708,29 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
   }
   uint32_t parity = 0;
   bool stop = false;  // a bounded wait ran out: no further work, no flush
-  auto prefetch = [&](int f_, int u_, int s_) {
+  // the columns of units ug_ UPW .. ug_ UPW + UPW - 1 of segment s_ of FFT pair f_: unit w's
+  // column c and mirror N1 - c (0 and N1/2 for unit 0) at region columns 2w, 2w + 1
+  auto prefetch = [&](int f_, int ug_, int s_) {
     const float2* col = a.scratch + ((size_t)s_ * a.n_fpair + f_) * N1 * N2;
-    const int c0 = (u_ == 0) ? 0 : u_, c1 = (u_ == 0) ? N1 / 2 : N1 - u_;
-    bulk_load2_elect(bar, smem_addr(region), col + (size_t)c0 * N2, smem_addr(region + N2), col + (size_t)c1 * N2,
-                     (uint32_t)(N2 * sizeof(float2)));
+    if constexpr (UPW == 1) {
+      const int u_ = ug_;
+      const int c0 = (u_ == 0) ? 0 : u_, c1 = (u_ == 0) ? N1 / 2 : N1 - u_;
+      bulk_load2_elect(bar, smem_addr(region), col + (size_t)c0 * N2, smem_addr(region + N2), col + (size_t)c1 * N2,
+                       (uint32_t)(N2 * sizeof(float2)));
+    } else {
+      if (lane == 0) {
+        constexpr uint32_t bytes = (uint32_t)(N2 * sizeof(float2));
+        mbar_expect_tx(bar, 2 * UPW * bytes);
+        sfor<0, UPW>([&](auto w_) {
+          constexpr int w = decltype(w_)::value;
+          const int u_ = ug_ * UPW + w;
+          const int c0 = (u_ == 0) ? 0 : u_, c1 = (u_ == 0) ? N1 / 2 : N1 - u_;
+          bulk_load(bar, smem_addr(region + (2 * w) * (N2 + PL::PADC)), col + (size_t)c0 * N2, bytes);
+          bulk_load(bar, smem_addr(region + (2 * w + 1) * (N2 + PL::PADC)), col + (size_t)c1 * N2, bytes);
+        });
+      }
+      __syncwarp();
+    }
   };
 
   // lane roles: step 1 (uw, e, q2); step 2 (uw, j)
@@ -765,7 +792,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
       if (r_begin < r_end) {
         fence_async_shared();  // the previous item's shared reads of the region come first
         __syncwarp();
-        prefetch(f, u, r_begin);
+        prefetch(f, ug, r_begin);
       }
     }
     // after the region is free: start the next segment's copy
@@ -774,7 +801,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
         if (rnd_ + 1 < r_end) {
           fence_async_shared();  // this warp's shared reads before the copy's writes
           __syncwarp();
-          prefetch(f, u, rnd_ + 1);
+          prefetch(f, ug, rnd_ + 1);
         }
       }
     };
@@ -794,7 +821,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
         if (stop) break;
         sfor<0, P>([&](auto t_) {
           constexpr int t = decltype(t_)::value;
-          v[ct::bitrev(t, P)] = region[e1 * N2 + q2 + Q2 * t];
+          v[ct::bitrev(t, P)] = region[(uw * 2 + e1) * (N2 + PL::PADC) + q2 + Q2 * t];
         });
         __syncwarp();  // every lane has its column before the transpose overwrites the region
       } else {
