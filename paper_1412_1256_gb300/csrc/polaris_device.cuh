@@ -355,11 +355,11 @@ struct Plan {
   static constexpr int TTW = ((2 * P + 15) / 16) * 16;     // and the lane's column twiddles W_N^{b u}
   static constexpr int TCOLS2 = pow2_at_least((WARPS / 4) * (TACC + TTW), 32);
   // phase 2 prefetches the next segment's 2 UPW columns (each unit's column and its mirror)
-  // into the warp's region with bulk copies when a warp holds at most four units of one
-  // segment (N2 >= 128: 2^13 and up).  Column g sits at g (N2 + PADC): the Q2-lane groups
-  // of a half-warp then start on distinct bank pairs.
+  // into the warp's region with bulk copies when a warp holds at most eight units of one
+  // segment (N2 >= 64: 2^11 and up).  Column g sits at g (N2 + PADC): the Q2-lane groups
+  // of a half-warp then start on distinct bank pairs (PADC 8-byte values, 16-byte aligned).
   static constexpr int PADC = UPW > 1 ? Q2 : 0;
-  static constexpr bool PF2 = (SL == 1) && (UPW <= 4) && (2 * UPW * (N2 + PADC) <= REGION2);
+  static constexpr bool PF2 = (SL == 1) && (UPW <= 8) && (PADC * 8) % 16 == 0 && (2 * UPW * (N2 + PADC) <= REGION2);
   // regions | W_N2 table | tensor-memory slot (16 B) | one mbarrier per warp
   static constexpr size_t SMEM2 = sizeof(float2) * ((size_t)WARPS * REGION2 + TWT) + 16 + 8 * WARPS;
 
