@@ -347,7 +347,10 @@ struct Plan {
   static constexpr int UGW = UPW > UPS ? 1 : UPS / UPW;    // unit groups per pair-segment
   static constexpr bank::Ld2 L2 = bank::p2_layout(P, Q2);
   static constexpr int LDQ2 = L2.a, LDE2 = L2.b;
-  static constexpr int REGION2 = (2 * UPW * LDE2 > 2 * UPW * N2) ? 2 * UPW * LDE2 : 2 * UPW * N2;
+  // prefetch column padding (see PF2): Q2 values, at least two (16-byte aligned copies)
+  static constexpr int PADC = UPW > 1 ? (Q2 >= 2 ? Q2 : 2) : 0;
+  static constexpr int REGION2 =
+      (2 * UPW * LDE2 > 2 * UPW * (N2 + PADC)) ? 2 * UPW * LDE2 : 2 * UPW * (N2 + PADC);
   // W_N2^k at k + k/32.  (A lane-contiguous [q][p] table has fewer bank conflicts but
   // measured slower in this kernel.)
   static constexpr int TWT = N2 + N2 / 32 + 1;
@@ -355,11 +358,11 @@ struct Plan {
   static constexpr int TTW = ((2 * P + 15) / 16) * 16;     // and the lane's column twiddles W_N^{b u}
   static constexpr int TCOLS2 = pow2_at_least((WARPS / 4) * (TACC + TTW), 32);
   // phase 2 prefetches the next segment's 2 UPW columns (each unit's column and its mirror)
-  // into the warp's region with bulk copies when a warp holds at most eight units of one
-  // segment (N2 >= 64: 2^11 and up).  Column g sits at g (N2 + PADC): the Q2-lane groups
-  // of a half-warp then start on distinct bank pairs (PADC 8-byte values, 16-byte aligned).
-  static constexpr int PADC = UPW > 1 ? Q2 : 0;
-  static constexpr bool PF2 = (SL == 1) && (UPW <= 8) && (PADC * 8) % 16 == 0 && (2 * UPW * (N2 + PADC) <= REGION2);
+  // into the warp's region with bulk copies when a warp holds the units of one segment
+  // (2^9 and up).  Column g sits at g (N2 + PADC): the Q2-lane groups of a half-warp then
+  // start on distinct bank pairs (two-way conflicts at Q2 = 1, where the pad is 2).
+  static constexpr bool PF2 = (SL == 1) && (UPW <= 16) && (PADC * 8) % 16 == 0 && (N2 * 8) % 16 == 0 &&
+                              (2 * UPW * (N2 + PADC) <= REGION2);
   // regions | W_N2 table | tensor-memory slot (16 B) | one mbarrier per warp
   static constexpr size_t SMEM2 = sizeof(float2) * ((size_t)WARPS * REGION2 + TWT) + 16 + 8 * WARPS;
 
