@@ -73,7 +73,9 @@ __global__ void k_unpack(const uint32_t* __restrict__ w, long long n, float* __r
 // Each slot holds sum |S|^2, |D|^2 and Re, Im of i S conj(D) with S = 2X, D = 2iY.
 // ---------------------------------------------------------------------------------------
 struct ReadoutArgs {
-  void* acc;  // read, then cleared
+  void* acc;  // read, then cleared: [copies][FFT pair][native slot]
+  int copies;             // accumulator copies summed per slot (0 or 1: one)
+  long long copy_stride;  // slots per copy
   int fp64;
   int N1, N2, UPS, nbin, native;
   int fa[kMaxIF], fb[kMaxIF], fcorr[kMaxIF];
@@ -128,10 +130,18 @@ __global__ void __launch_bounds__(kReadoutThreads) k_readout(ReadoutArgs a) {
     slot[i] = idx;
     sidx[i] = dd * (CT + 1) + cc;
     if (a.fp64) {
-      const double4 w = reinterpret_cast<const double4*>(a.acc)[fo + idx];
+      double4 w = reinterpret_cast<const double4*>(a.acc)[fo + idx];
+      for (int k = 1; k < a.copies; ++k) {
+        const double4 x = reinterpret_cast<const double4*>(a.acc)[(size_t)k * a.copy_stride + fo + idx];
+        w = make_double4(w.x + x.x, w.y + x.y, w.z + x.z, w.w + x.w);
+      }
       v[i] = make_float4((float)(0.25 * w.x), (float)(0.25 * w.y), (float)(0.25 * w.z), (float)(0.25 * w.w));
     } else {
-      const float4 w = reinterpret_cast<const float4*>(a.acc)[fo + idx];
+      float4 w = reinterpret_cast<const float4*>(a.acc)[fo + idx];
+      for (int k = 1; k < a.copies; ++k) {
+        const float4 x = reinterpret_cast<const float4*>(a.acc)[(size_t)k * a.copy_stride + fo + idx];
+        w = make_float4(w.x + x.x, w.y + x.y, w.z + x.z, w.w + x.w);
+      }
       v[i] = make_float4(0.25f * w.x, 0.25f * w.y, 0.25f * w.z, 0.25f * w.w);
     }
     if (c > N1 / 2) v[i].w = -v[i].w;  // mirror column: conjugate
@@ -139,8 +149,11 @@ __global__ void __launch_bounds__(kReadoutThreads) k_readout(ReadoutArgs a) {
 #pragma unroll
   for (int i = 0; i < PT; ++i) {
     if (slot[i] < 0) continue;
-    if (a.fp64) reinterpret_cast<double4*>(a.acc)[fo + slot[i]] = make_double4(0.0, 0.0, 0.0, 0.0);
-    else reinterpret_cast<float4*>(a.acc)[fo + slot[i]] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = 0; k < (a.copies > 1 ? a.copies : 1); ++k) {
+      const size_t o = (size_t)k * a.copy_stride + fo + slot[i];
+      if (a.fp64) reinterpret_cast<double4*>(a.acc)[o] = make_double4(0.0, 0.0, 0.0, 0.0);
+      else reinterpret_cast<float4*>(a.acc)[o] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
     tile[sidx[i]] = v[i];
   }
   __syncthreads();
@@ -238,6 +251,7 @@ struct polaris_spec {
   int n_pair = 0, n_fpair = 0;
   int fa[kMaxIF], fb[kMaxIF], fcorr[kMaxIF];
   int max_batch = 0;
+  int acc_copies = 1;
   float* d_taps = nullptr;
   float2* d_tw = nullptr;
   void* d_acc = nullptr;
@@ -496,7 +510,19 @@ extern "C" int spectrometer_create(const polaris_config* cfg, polaris_spec** out
   s->slab_half = (size_t)s->max_batch * nf * N;
   s->carry_words_cap = N / spw;               // carried samples < N
   s->stage_words_cap = 2 * N / spw;           // staging < carry + N samples
-  const size_t acc_bytes = (size_t)nf * s->native * 4 * (s->accum_fp64 ? 8 : 4);
+  // Accumulator copies.  Phase 2 gives each warp one range of segments of one (pair, unit
+  // group) and adds the range's sums into every slot of the group once; at small N (few
+  // groups, ranges of a few segments) a slot would take ~1200 atomic adds per pass, which
+  // serialise per address.  Range r adds into copy r % K (about 64 adds per copy); the
+  // readout sums the copies.
+  {
+    const int P = plan_p(logn), Q2 = s->N2 / P, UPW = 16 / Q2;
+    const int UGW = UPW > s->UPS ? 1 : s->UPS / UPW;
+    const long long warps = 2LL * s->num_sms * 8;  // phase-2 warps resident: two 8-warp CTAs per SM
+    const long long nrg = warps / ((long long)nf * UGW);
+    s->acc_copies = (int)(nrg / 64 < 1 ? 1 : (nrg / 64 > 16 ? 16 : nrg / 64));
+  }
+  const size_t acc_bytes = (size_t)s->acc_copies * nf * s->native * 4 * (s->accum_fp64 ? 8 : 4);
   const size_t bytes_tw = (size_t)s->N2 * (s->UPS + 1) * sizeof(float2);
   const size_t bytes_scratch = 2 * (size_t)s->max_batch * nf * N * sizeof(float2);
   const size_t bytes_carry = (size_t)c.n_if * s->carry_words_cap * 4;
@@ -701,6 +727,7 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
   a.scratch = s->d_scratch;
   a.tw = s->d_tw;
   a.acc = s->d_acc;
+  a.acc_copies = s->acc_copies;
   a.fp64 = s->accum_fp64;
   a.bits = s->bits;
   a.num_sms = s->num_sms;
@@ -776,6 +803,8 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
 static int fill_readout(polaris_spec* s, const polaris_stokes_params* prm, ReadoutArgs& r) {
   memset(&r, 0, sizeof r);
   r.acc = s->d_acc;
+  r.copies = s->acc_copies;
+  r.copy_stride = (long long)s->n_fpair * s->native;
   r.err = s->d_err;
   r.fp64 = s->accum_fp64;
   r.N1 = s->N1;
@@ -1141,6 +1170,7 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
   a.wait_limit = g_wait_limit;
   a.tw = tw;
   a.acc = acc;
+  a.acc_copies = 1;
   a.fp64 = c.accum_fp64 ? 1 : 0;
   a.bits = c.bits;
   a.num_sms = num_sms;
@@ -1154,6 +1184,8 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
   ReadoutArgs r;
   memset(&r, 0, sizeof r);
   r.acc = acc;
+  r.copies = 1;
+  r.copy_stride = (long long)nf * native;
   r.err = d_err;
   r.fp64 = a.fp64;
   r.N1 = N1;

@@ -74,7 +74,8 @@ struct BatchArgs {
   const float* taps;    // window taps (N) or nullptr for the rectangular window
   float2* scratch;      // slab [nseg * n_fpair][N1][N2]: row c (phase-1 output index), b contiguous
   const float2* tw;     // [UPS + 1][N2]: W_N^{b u} (unit-major)
-  void* acc;            // native accumulators [n_fpair][N/2 + 1] of float4 (or double4 if fp64)
+  void* acc;            // native accumulators [acc_copies][n_fpair][N/2 + 1] of float4 (double4 if fp64)
+  int acc_copies;       // 1, or K: segment range r of a (pair, unit group) adds into copy r % K
   int fp64;
   int bits;
   int num_sms;
@@ -939,8 +940,9 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
       }
     }
     if (stop) break;
-    // flush this lane's sums into the integration accumulators (native order)
-    const size_t base = (size_t)f * PL::NATIVE;
+    // flush this lane's sums into the integration accumulators (native order; the range's copy)
+    const int copy = a.acc_copies > 1 ? rg % a.acc_copies : 0;
+    const size_t base = ((size_t)copy * a.n_fpair + f) * PL::NATIVE;
     sfor<0, (NACC + 3) / 4>([&](auto c_) {
       constexpr int cc = decltype(c_)::value;
       float a16[16];
