@@ -95,6 +95,24 @@ def test_staged_sizes_every_width(pol, orc, logn, bits):
     assert_close(got, ref, [(0, 1)], TOL)
 
 
+@pytest.mark.parametrize("logn,fp64", [(10, False), (11, False), (12, True), (13, False)])
+def test_small_n_accumulator_copies_two_integrations(pol, orc, logn, fp64):
+    """Small N, where a pass gives each warp a range of a few segments and the ranges of a
+    (pair, unit group) add into several accumulator copies that the readout sums: two
+    integrations in a row on one handle (the second must not see the first's sums), enough
+    segments for many ranges per group, FP32 and FP64 accumulation."""
+    n_fft, bits, nseg = 1 << logn, 2, 600 if logn <= 11 else 160
+    n = n_fft * nseg
+    with pol.Spectrometer(4, bits, n_fft, accum_fp64=fp64) as sp:
+        for k in range(2):
+            packed = _random_streams(3000 + 10 * logn + k, 4, n, bits)
+            sp.feed(packed, n)
+            got = sp.integrate()
+            ref = _oracle(orc, packed, bits, n_fft, n)
+            assert got["n_segments"] == nseg
+            assert_close(got, ref, [(0, 2), (1, 3)], TOL)
+
+
 def test_paper_config_one_integration(pol, orc):
     """4 IFs, 2-bit, N = 131072, 61 segments (one 1-s integration), three-line spectrum."""
     packed, meta = synth.config_paper(n_segments=61)
