@@ -8,10 +8,14 @@ crosses and Stokes I, Q, U, V of both pairs - i.e. 4 x 61 x 131072 =
 
   value  device-resident input (a 480 MB ring of distinct seconds, larger than
          L2, so every step reads its input from HBM), feed + integrate to device
-         outputs through the C ABI, timed with CUDA events on the launching stream.
+         outputs through the C ABI, timed with CUDA events (forked from and joined
+         back into the launching stream).  Consecutive steps are independent 1-s
+         integrations; they alternate over --handles spectrometer handles on as many
+         streams, as a streaming caller would run them, so that one integration's
+         phase-2 tail and readout overlap the next one's phase 1.
   e2e    the same metric through the C ABI with pinned HOST buffers: host->device
          copy of the step's packed input and device->host copy of its autos,
-         crosses and Stokes inside the timed region.
+         crosses and Stokes inside the timed region (--e2e-handles handles).
 
 --impl reference times the FP64 CPU oracle on this machine's host cores on a
 bounded sample of the same workload (the reference arm; there is no upstream code).
@@ -56,6 +60,7 @@ CONFIG = {
     "samples_per_step": SAMPLES_PER_STEP,
     "l2": "inputs larger than L2: 60 distinct seconds (480 MB ring) cycled, each step reads another second",
 }
+DEFAULT_HANDLES, DEFAULT_E2E_HANDLES = 3, 4
 
 
 # ------------------------------------------------------------------------------------------
@@ -564,31 +569,49 @@ def run_ours(args, rank, world, local_rank, dist):
     stokes = torch.empty((N_PAIR, 4, NBIN), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     sp = polaris.Spectrometer(N_IF, BITS, N_FFT, device=local_rank, max_batch_segments=args.batch_segments)
+    # the timed steps alternate over H handles, each with its own stream and outputs
+    # (independent integrations); handle 0 also serves the per-kernel profiling pass
+    H = max(1, args.handles)
+    handles = [(sp, stream, (autos, cross, stokes))]
+    for _ in range(H - 1):
+        handles.append((polaris.Spectrometer(N_IF, BITS, N_FFT, device=local_rank,
+                                             max_batch_segments=args.batch_segments),
+                        torch.cuda.Stream(dev),
+                        (torch.empty_like(autos), torch.empty_like(cross), torch.empty_like(stokes))))
 
-    def step(i):
+    def step(i, h=None):
+        sph, sth, outs = handles[i % H if h is None else h]
         sec = ring[i % ring_n]
-        sp.feed([sec[j] for j in range(N_IF)], SAMPLES_PER_IF, on_device=True, stream=stream)
-        return sp.integrate_device(autos, cross, stokes, stream=stream)
+        sph.feed([sec[j] for j in range(N_IF)], SAMPLES_PER_IF, on_device=True, stream=sth)
+        return sph.integrate_device(*outs, stream=sth)
 
     def barrier():
         if dist is not None:
             dist.barrier()
 
-    for i in range(args.warmup):
+    for i in range(max(args.warmup, H)):
         assert step(i) == SEGS
     torch.cuda.synchronize(dev)
     barrier()
     torch.cuda.synchronize(dev)
-    l0 = sp.kernel_launches()
+    l0 = sum(h[0].kernel_launches() for h in handles)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local_rank) as clk:
         e0.record(stream)
+        for _, sth, _ in handles[1:]:
+            sth.wait_event(e0)  # fork
         for i in range(args.steps):
             step(args.warmup + i)
+        for _, sth, _ in handles[1:]:
+            ev = torch.cuda.Event()
+            ev.record(sth)
+            stream.wait_event(ev)  # join
         e1.record(stream)
         torch.cuda.synchronize(dev)
     barrier()
-    launches = sp.kernel_launches() - l0
+    launches = sum(h[0].kernel_launches() for h in handles) - l0
+    for hd in handles[1:]:
+        hd[0].close()
     t_ms = e0.elapsed_time(e1)
     t_max = slowest(dist, t_ms)
     value = whole_job_rate(world, args.steps, SAMPLES_PER_STEP, t_max * 1e-3)
@@ -597,25 +620,26 @@ def run_ours(args, rank, world, local_rank, dist):
     sp.set_profiling(True)
     prof_steps = max(3, min(args.steps, 50))
     for i in range(prof_steps):
-        step(i)
+        step(i, 0)
     torch.cuda.synchronize(dev)
     kt = sp.kernel_times()
     sp.set_profiling(False)
 
     # e2e through the C ABI with pinned host buffers: every step copies its input from
-    # pinned host memory (feed with host pointers) and reads its spectra back into pinned
-    # host memory (integrate_async: readout and copies queued in one call).  The feed returns
-    # once its input is read (host_async measured slower here: the host then runs far enough
-    # ahead for the two handles' kernels to overlap and compete for the SMs).  Two spectrometer handles on two streams take alternate steps, so that
-    # step i+1's host-to-device copy overlaps step i's kernels (a streaming caller's
-    # pattern); the host waits for step i's outputs only after queueing step i+1.
+    # pinned host memory (feed with host pointers, asynchronous mode: the copy is queued and
+    # the call returns; the pinned buffers stay unchanged) and reads its spectra back into
+    # pinned host memory (integrate_async: readout and copies queued in one call).  L
+    # spectrometer handles on L streams take steps in turn, so that copies and kernels of
+    # consecutive integrations overlap (a streaming caller's pattern); the host waits for
+    # step i's outputs after queueing step i + L - 1.
     e2e_value = None
     if not args.no_e2e:
         n_host = min(len(unique), 4)
         pinned = [torch.from_numpy(unique[i]).pin_memory() for i in range(n_host)]
         host = [p.numpy().view(np.uint32) for p in pinned]
         lanes = []
-        for k in range(2):
+        L = max(2, args.e2e_handles)
+        for k in range(L):
             spk = sp if k == 0 else polaris.Spectrometer(N_IF, BITS, N_FFT, device=local_rank,
                                                          max_batch_segments=args.batch_segments)
             stk = torch.cuda.Stream(dev)
@@ -626,31 +650,34 @@ def run_ours(args, rank, world, local_rank, dist):
             lanes.append((spk, stk, dev_out, host_out, torch.cuda.Event()))
 
         def e2e_issue(i):
-            spk, stk, dev_out, host_out, done = lanes[i % 2]
-            spk.feed([host[i % n_host][j] for j in range(N_IF)], SAMPLES_PER_IF, on_device=False, stream=stk)
+            spk, stk, dev_out, host_out, done = lanes[i % L]
+            spk.feed([host[i % n_host][j] for j in range(N_IF)], SAMPLES_PER_IF, on_device=False, stream=stk,
+                     host_async=True)
             nseg = spk.integrate_async(dict(zip(("autos", "cross", "stokes"), host_out)), stream=stk)
             done.record(stk)
             return nseg
 
         def e2e_wait(i):
-            lanes[i % 2][4].synchronize()
+            lanes[i % L][4].synchronize()
 
-        for i in range(4):
+        for i in range(2 * L):
             assert e2e_issue(i) == SEGS
             e2e_wait(i)
         e2e_steps = max(3, min(args.steps, args.e2e_steps))
         torch.cuda.synchronize(dev)
         barrier()
         t0 = time.perf_counter()
-        assert e2e_issue(0) == SEGS
+        for i in range(min(L - 1, e2e_steps)):
+            assert e2e_issue(i) == SEGS
         for i in range(e2e_steps):
-            if i + 1 < e2e_steps:
-                assert e2e_issue(i + 1) == SEGS
+            if i + L - 1 < e2e_steps:
+                assert e2e_issue(i + L - 1) == SEGS
             e2e_wait(i)  # step i's spectra are in host memory
         torch.cuda.synchronize(dev)
         dt = slowest(dist, time.perf_counter() - t0)
         e2e_value = whole_job_rate(world, e2e_steps, SAMPLES_PER_STEP, dt)
-        lanes[1][0].close()
+        for ln in lanes[1:]:
+            ln[0].close()
 
     # variants of the same workload (NEXT-4): 50% overlap (hop = N/2, Sec. 3.1) and the
     # code-histogram statistics (Sec. 2 bit distribution), each through the same API
@@ -756,6 +783,10 @@ def run_ours(args, rank, world, local_rank, dist):
                 "d2h_bytes_per_step": D2H_BYTES},
         "gpu_launches": launches,
         "clocks": clocks,
+        "pipeline": {"handles": H, "e2e_handles": None if args.no_e2e else max(2, args.e2e_handles),
+                     "note": "consecutive steps (independent 1-s integrations) alternate over this many "
+                             "spectrometer handles, each on its own stream; per-kernel times come from a "
+                             "separate pass of one handle on one stream"},
     }
     if variants is not None:
         for v in ("forward_loss", "forward_adjoint"):
@@ -784,7 +815,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ring", type=int, default=60, help="distinct seconds of input kept on the device")
     ap.add_argument("--unique", type=int, default=2, help="distinct generated seconds (tiled over the ring)")
-    ap.add_argument("--e2e-steps", type=int, default=40)
+    ap.add_argument("--e2e-steps", type=int, default=200)
+    ap.add_argument("--handles", type=int, default=DEFAULT_HANDLES,
+                    help="spectrometer handles (and streams) the timed steps alternate over")
+    ap.add_argument("--e2e-handles", type=int, default=DEFAULT_E2E_HANDLES,
+                    help="handles (and streams) of the end-to-end loop")
     ap.add_argument("--cpu-segs", type=int, default=61)
     ap.add_argument("--ref-seconds", type=float, default=60.0,
                     help="reference arm: about this many seconds of oracle work over warmup + steps")
