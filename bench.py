@@ -685,43 +685,61 @@ def run_ours(args, rank, world, local_rank, dist):
     if not args.no_variants:
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-        def timed(spv, nsteps):
-            def stepv(i):
-                sec = ring[i % ring_n]
-                spv.feed([sec[j] for j in range(N_IF)], SAMPLES_PER_IF, on_device=True, stream=stream)
-                return spv.integrate_device(autos, cross, stokes, stream=stream)
+        def timed(make, nsteps):
+            """nsteps steps alternating over H handles made by make(), as in the main timing;
+            returns (ms per step, segments of the last step, the handles, warm-up steps)."""
+            hs = [(make(), stream if k == 0 else torch.cuda.Stream(dev),
+                   (autos, cross, stokes) if k == 0 else
+                   (torch.empty_like(autos), torch.empty_like(cross), torch.empty_like(stokes))) for k in range(H)]
 
-            for i in range(3):
+            def stepv(i):
+                spv, st, outs = hs[i % H]
+                sec = ring[i % ring_n]
+                spv.feed([sec[j] for j in range(N_IF)], SAMPLES_PER_IF, on_device=True, stream=st)
+                return spv.integrate_device(*outs, stream=st)
+
+            warm = max(3, H)
+            for i in range(warm):
                 stepv(i)
             torch.cuda.synchronize(dev)
             segs = 0
             ev0.record(stream)
+            for _, st, _ in hs[1:]:
+                st.wait_event(ev0)
             for i in range(nsteps):
-                segs = stepv(3 + i)
+                segs = stepv(warm + i)
+            for _, st, _ in hs[1:]:
+                evj = torch.cuda.Event()
+                evj.record(st)
+                stream.wait_event(evj)
             ev1.record(stream)
             torch.cuda.synchronize(dev)
-            return ev0.elapsed_time(ev1) / nsteps, segs
+            return ev0.elapsed_time(ev1) / nsteps, segs, hs, warm
 
         nv = max(10, min(args.steps, 100))
         variants = {}
-        with polaris.Spectrometer(N_IF, BITS, N_FFT, hop=N_FFT // 2, device=local_rank) as spo:
-            ms, segs = timed(spo, nv)
+        ms, segs, hs, _ = timed(lambda: polaris.Spectrometer(N_IF, BITS, N_FFT, hop=N_FFT // 2, device=local_rank), nv)
+        for hd in hs:
+            hd[0].close()
         variants["overlap_50"] = {"hop": N_FFT // 2, "segments_per_step": segs, "ms_per_step": ms,
                                   "value": world * SAMPLES_PER_STEP / (ms * 1e-3) / 1e6, "unit": "Msample/s",
-                                  "steps": nv}
-        with polaris.Spectrometer(N_IF, BITS, N_FFT, device=local_rank, code_stats=True) as sps:
-            ms, segs = timed(sps, nv)
-            sps.set_profiling(True)
-            for i in range(10):
-                sps.feed([ring[i % ring_n][j] for j in range(N_IF)], SAMPLES_PER_IF, on_device=True, stream=stream)
-                sps.integrate_device(autos, cross, stokes, stream=stream)
-            torch.cuda.synchronize(dev)
-            kh = sps.kernel_times()["code_histogram"]
-            sps.set_profiling(False)
-            h = sps.code_histogram()
-            assert int(h.sum()) == N_IF * N_FFT * SEGS * (3 + nv + 10)
+                                  "steps": nv, "handles": H}
+        ms, segs, hs, warm = timed(lambda: polaris.Spectrometer(N_IF, BITS, N_FFT, device=local_rank, code_stats=True),
+                                   nv)
+        sps = hs[0][0]
+        sps.set_profiling(True)
+        for i in range(10):
+            sps.feed([ring[i % ring_n][j] for j in range(N_IF)], SAMPLES_PER_IF, on_device=True, stream=stream)
+            sps.integrate_device(autos, cross, stokes, stream=stream)
+        torch.cuda.synchronize(dev)
+        kh = sps.kernel_times()["code_histogram"]
+        sps.set_profiling(False)
+        counted = sum(int(hd[0].code_histogram().sum()) for hd in hs)
+        assert counted == N_IF * N_FFT * SEGS * (warm + nv + 10)
+        for hd in hs:
+            hd[0].close()
         variants["code_stats"] = {"ms_per_step": ms, "value": world * SAMPLES_PER_STEP / (ms * 1e-3) / 1e6,
-                                  "unit": "Msample/s", "steps": nv,
+                                  "unit": "Msample/s", "steps": nv, "handles": H,
                                   "histogram_kernel_ms": kh[0] / kh[1] if kh[1] else None}
         variants["batch_graph"] = batch_graph_variant(torch, polaris, dev, local_rank, world)
         variants["adjoint"] = adjoint_variant(torch, polaris, dev, local_rank, world)
