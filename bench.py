@@ -825,6 +825,48 @@ def run_ours(args, rank, world, local_rank, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args, local_rank):
+    """Throughput against N (--sweep LOGN,...): 4 IFs of --sweep-bits-bit samples, rectangular
+    window, about 8 M samples per IF per step (whole segments), one handle on one stream,
+    the library's default batch, input cycling over 8 device buffers (which fit in L2);
+    prints one JSON line {"sweep": {log2 N: Msample/s}, ...}.  Not the benchmark line."""
+    import torch
+
+    from paper_1412_1256_gb300 import polaris
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    polaris.load()
+    bits, n_if, reps = args.sweep_bits, 4, args.sweep_reps
+    out = {}
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1256)
+    for logn in [int(x) for x in args.sweep.split(",") if x]:
+        n_fft = 1 << logn
+        n = max(1, (8 << 20) // n_fft) * n_fft
+        ring = [[torch.randint(-2**31, 2**31 - 1, (n * bits // 32,), dtype=torch.int32, device=dev, generator=gen)
+                 for _ in range(n_if)] for _ in range(8)]
+        nb = n_fft // 2 + 1
+        outs = (torch.empty((n_if, nb), device=dev), torch.empty((n_if // 2, nb, 2), device=dev),
+                torch.empty((n_if // 2, 4, nb), device=dev))
+        st = torch.cuda.Stream(dev)
+        with polaris.Spectrometer(n_if, bits, n_fft, device=local_rank) as sp:
+            for i in range(3):
+                sp.feed(ring[i % 8], n, on_device=True, stream=st)
+                sp.integrate_device(*outs, stream=st)
+            st.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for i in range(reps):
+                sp.feed(ring[i % 8], n, on_device=True, stream=st)
+                sp.integrate_device(*outs, stream=st)
+            e1.record(st)
+            st.synchronize()
+        out[logn] = n_if * n * reps / (e0.elapsed_time(e1) * 1e-3) / 1e6
+        del ring
+    print(json.dumps({"sweep": out, "unit": "Msample/s", "bits": bits, "n_if": n_if, "reps": reps}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -848,7 +890,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the overlap / code-statistics variants")
+    ap.add_argument("--sweep", default="", help="comma-separated log2 N: print the throughput against N instead")
+    ap.add_argument("--sweep-bits", type=int, default=2)
+    ap.add_argument("--sweep-reps", type=int, default=20)
     args = ap.parse_args()
+    if args.sweep:
+        run_sweep(args, int(os.environ.get("LOCAL_RANK", "0")))
+        return
     if args.warmup < 3:
         args.warmup = 3
     world = int(os.environ.get("WORLD_SIZE", "1"))
