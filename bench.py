@@ -131,7 +131,7 @@ class ClockSampler:
                0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
                0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting"}
 
-    def __init__(self, cuda_index: int, period_s: float = 0.002):
+    def __init__(self, cuda_index: int, period_s: float = 0.0005):
         self.samples, self.reasons, self.max_mhz = [], 0, None
         self.period, self._stop = period_s, threading.Event()
         self.ok = False
