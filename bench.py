@@ -60,7 +60,7 @@ CONFIG = {
     "samples_per_step": SAMPLES_PER_STEP,
     "l2": "inputs larger than L2: 60 distinct seconds (480 MB ring) cycled, each step reads another second",
 }
-DEFAULT_HANDLES, DEFAULT_E2E_HANDLES = 3, 4
+DEFAULT_HANDLES, DEFAULT_E2E_HANDLES = 3, 6
 
 
 # ------------------------------------------------------------------------------------------
