@@ -108,7 +108,12 @@ typedef struct {
 
 /* Create a spectrometer.  Allocates all device state (accumulators, twiddle and
  * window tables, scratch).  Returns POLARIS_EINVAL for invalid config (out is
- * untouched), POLARIS_ENOMEM / POLARIS_ECUDA on allocation / CUDA failure. */
+ * untouched), POLARIS_ENOMEM / POLARIS_ECUDA on allocation / CUDA failure.
+ * A handle runs its integrations one after another in stream order.  Independent
+ * integrations (consecutive seconds of a stream, other IF sets) kept in flight on
+ * separate handles and CUDA streams overlap on the GPU: one integration's transform
+ * runs beside another's correlation (three handles: about 1.3x one handle's rate at
+ * N = 2^17). */
 int spectrometer_create(const polaris_config* cfg, polaris_spec** out);
 
 /* Feed n_samples_per_if new samples of every IF stream and accumulate all whole
