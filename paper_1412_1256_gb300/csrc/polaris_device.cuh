@@ -95,41 +95,37 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {  // conj(a) * b
 }
 
 // Radix-2 DIT butterfly a' = a + W b, b' = a - W b with W = e^{-2 pi i J / SPAN}
-// (compile-time).  W = 1 and W = -i cost 4 adds; other W use the cosine-factored form
-// a +- w (b x-part - t b y-part, ...) with |t| <= 1: 6 FMAs.
+// (compile-time).  W = 1 and W = -i cost two packed adds/FMAs; other W use the
+// cosine-factored form a +- w (b x-part - t b y-part, ...) with |t| <= 1: three packed FMAs.
+// The packed two-wide FP32 operations (__ffma2_rn, __fadd2_rn) round each component once,
+// as fmaf and a scalar add do, so the results equal the scalar form bit for bit with half
+// the FP32 instructions, which both issue-bound transform kernels need.
 template <int J, int SPAN>
 __device__ __forceinline__ void dit_bfly(float2& a, float2& b) {
   if constexpr (J == 0) {
-    const float tx = b.x, ty = b.y;
-    b.x = a.x - tx;
-    b.y = a.y - ty;
-    a.x += tx;
-    a.y += ty;
+    const float2 t = b;
+    b = __ffma2_rn(t, make_float2(-1.f, -1.f), a);  // a - t: an exact product, one rounding
+    a = __fadd2_rn(a, t);
   } else if constexpr (4 * J == SPAN) {  // W = -i: W b = (b.y, -b.x)
-    const float tx = b.y, ty = -b.x;
-    b.x = a.x - tx;
-    b.y = a.y - ty;
-    a.x += tx;
-    a.y += ty;
+    const float2 s = make_float2(b.y, b.x);
+    b = __ffma2_rn(s, make_float2(-1.f, 1.f), a);  // (a.x - b.y, a.y + b.x)
+    a = __ffma2_rn(s, make_float2(1.f, -1.f), a);  // (a.x + b.y, a.y - b.x)
   } else {
     constexpr ct::CS cs = ct::cossin2pi(J, SPAN);
     constexpr double wr = cs.c, wi = -cs.s;  // W = wr + i wi
     if constexpr (ct::dabs(wr) >= ct::dabs(wi)) {
       constexpr float r = (float)(wi / wr), sc = (float)wr;
-      // W b = wr * ((b.x - r b.y) + i (b.y + r b.x))
-      const float ux = fmaf(-r, b.y, b.x), uy = fmaf(r, b.x, b.y);
-      b.x = fmaf(-sc, ux, a.x);
-      b.y = fmaf(-sc, uy, a.y);
-      a.x = fmaf(sc, ux, a.x);
-      a.y = fmaf(sc, uy, a.y);
+      // W b = wr * u, u = (b.x - r b.y, b.y + r b.x)
+      const float2 u = __ffma2_rn(make_float2(b.y, b.x), make_float2(-r, r), b);
+      b = __ffma2_rn(make_float2(-sc, -sc), u, a);
+      a = __ffma2_rn(make_float2(sc, sc), u, a);
     } else {
       constexpr float r = (float)(wr / wi), sc = (float)wi;
-      // W b = wi * ((r b.x - b.y) + i (r b.y + b.x))
-      const float ux = fmaf(r, b.x, -b.y), uy = fmaf(r, b.y, b.x);
-      b.x = fmaf(-sc, ux, a.x);
-      b.y = fmaf(-sc, uy, a.y);
-      a.x = fmaf(sc, ux, a.x);
-      a.y = fmaf(sc, uy, a.y);
+      // W b = wi * u, u = (r b.x - b.y, r b.y + b.x); v = (-u.x, u.y), its first component
+      // negated exactly (round-to-nearest is symmetric)
+      const float2 v = __ffma2_rn(b, make_float2(-r, r), make_float2(b.y, b.x));
+      b = __ffma2_rn(make_float2(sc, -sc), v, a);
+      a = __ffma2_rn(make_float2(-sc, sc), v, a);
     }
   }
 }
