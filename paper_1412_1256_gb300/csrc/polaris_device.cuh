@@ -1,7 +1,8 @@
 // Device building blocks of the PolariS hot path for sm_103a:
 //   * compile-time twiddles (own octant-reduced Taylor series, FP64, rounded once to f32)
 //   * in-register radix-2 DIT transforms with the twiddle folded into the butterfly
-//     FMAs (cosine-factored form: a +- W b = a +- wr (b + (wi/wr) i b), 6 FMAs)
+//     FMAs (cosine-factored form: a +- W b = a +- wr (b + (wi/wr) i b), three packed
+//     two-wide FMAs)
 //   * the data-translation step (b-bit code -> float level, exact, no I2F)
 //   * the per-size two-phase plan N = N1 * N2.
 //
