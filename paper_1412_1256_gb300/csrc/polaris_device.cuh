@@ -186,6 +186,22 @@ __device__ __forceinline__ float decode_level_rot(uint32_t word, uint32_t rot) {
   }
 }
 
+// Both IFs' codes at one rotation into one complex sample, the two final subtractions as
+// one packed add (each component rounds as the scalar subtraction; exact here).
+template <int BITS>
+__device__ __forceinline__ float2 decode_pair_rot(uint32_t wa, uint32_t wb, uint32_t rot) {
+  const uint32_t ra = __funnelshift_r(wa, wa, rot), rb = __funnelshift_r(wb, wb, rot);
+  if constexpr (BITS == 8) {
+    return __fadd2_rn(make_float2(__uint_as_float((ra & 0xFFu) ^ 0x4B000080u), __uint_as_float((rb & 0xFFu) ^ 0x4B000080u)),
+                      make_float2(-8388736.0f, -8388736.0f));
+  } else {
+    constexpr uint32_t m = ((1u << BITS) - 1u) << 1;
+    constexpr float c = -(8388608.0f + (float)((1 << BITS) - 1));
+    return __fadd2_rn(make_float2(__uint_as_float((ra & m) | 0x4B000000u), __uint_as_float((rb & m) | 0x4B000000u)),
+                      make_float2(c, c));
+  }
+}
+
 // ----------------------------------------------------------------------------------------
 // two-phase plan: N = N1 * N2, n = N2 a + b (a row, b column), k = c + N1 d
 //   phase 1: for each column b, DFT-N1 over a (P points per thread, Q1 = N1/P threads)

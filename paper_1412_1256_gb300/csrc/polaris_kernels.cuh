@@ -633,14 +633,18 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
               wa = w.x;
               wb = w.y;
             }
-            float x = decode_level_rot<BITS>(wa, rot);
-            float y = HB ? decode_level_rot<BITS>(wb, rot) : 0.0f;
+            float2 z;
+            if constexpr (HB) {
+              z = decode_pair_rot<BITS>(wa, wb, rot);
+            } else {
+              z = make_float2(decode_level_rot<BITS>(wa, rot), 0.0f);
+            }
             if constexpr (TP) {
               const float tv = __ldg(a.taps + row * N2 + b);
-              x *= tv;
-              y *= tv;
+              z.x *= tv;
+              z.y *= tv;
             }
-            v[ct::bitrev(t, P)] = make_float2(x, y);
+            v[ct::bitrev(t, P)] = z;
           });
         };
         using T_ = std::true_type;
