@@ -47,7 +47,11 @@ enum {
   POLARIS_ECUDA = -3,    /* a CUDA call failed; the handle is now unusable   */
   POLARIS_ESTATE = -4,   /* wrong state (e.g. integrate with zero segments,
                             or a handle after a CUDA error)                  */
-  POLARIS_ETIMEOUT = -5  /* a bounded device-side wait ran out (see below)   */
+  POLARIS_ETIMEOUT = -5, /* a bounded device-side wait ran out (see below)   */
+  POLARIS_EBOUNDS = -6   /* bounds-checked build only (compiled with
+                            -DPOLARIS_CHECK): a kernel found an index outside
+                            its buffer, skipped that access and recorded it;
+                            outputs are NaN and the handle is unusable       */
 };
 
 /* window kinds (Sec. 3.1: rectangular online; Sec. 5: others possible) */
@@ -171,6 +175,22 @@ int spectrometer_n_pairs(const polaris_spec* s);
  * host floats `out`, on the GPU.  n must be a multiple of 32/bits. */
 int spectrometer_debug_unpack(polaris_spec* s, const void* packed, int64_t n, float* out);
 
+/* The data-translation step as the FFT kernel runs it from N = 2^13 up (Fig. 2 caption:
+ * integer codes to floats; Sec. 2: two IF streams enter one transform): that kernel stages
+ * each tile's packed words in shared memory and decodes every column at a per-column
+ * rotation, both IFs of a pair in one packed subtraction.  This call stages and decodes
+ * through that same device code, for bit-exact checks of the levels the transform sees.
+ *   packed_a, packed_b  host words of IF a and IF b of one FFT pair (packed_b NULL: a pair
+ *               without an IF b, decoded by the single-IF variant), n samples each;
+ *   n           a positive multiple of n_fft (whole segments, hop = n_fft);
+ *   layout      0: the interleaved stage of cp.async staging; 1: the dense [IF][row][word]
+ *               stage of TMA staging;
+ *   out_a, out_b  host floats, n each (out_b unused when packed_b is NULL).
+ * POLARIS_EINVAL when the FFT kernel does not stage at this handle's size and width (below
+ * 2^13, and 1-bit samples at 2^19 and 2^20: there it decodes as spectrometer_debug_unpack). */
+int spectrometer_debug_unpack_staged(polaris_spec* s, const void* packed_a, const void* packed_b, int64_t n,
+                                     int layout, float* out_a, float* out_b);
+
 /* Free all resources.  NULL is ignored. */
 void spectrometer_destroy(polaris_spec* s);
 
@@ -192,30 +212,34 @@ int spectrometer_kernel_times(polaris_spec* s, double* ms, int64_t* launches, in
 
 /* One integration without any device allocation.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when they need a
- * spectrum -- code running while a CUDA graph is being captured (cudaMalloc cannot be
- * captured), real-time loops in which cudaMalloc/cudaFree would synchronise the device
+ * spectrum -- real-time loops in which cudaMalloc/cudaFree would synchronise the device
  * and miss the sampler's deadline, and host frameworks that own all device memory
- * through their own pool.  It computes the same autos, crosses and Stokes as
- * create + feed + integrate_device for the whole segments of one input block
- * (samples after the last whole segment are ignored; nothing is carried), but it keeps
- * no handle: its scratch slab, accumulators, twiddles and window taps live in one
- * static device array of 32 MiB (POLARIS_NOALLOC_BYTES), which every GPU that loads
- * this library holds until the process exits.
- *   cfg         as for spectrometer_create (taps, if any, are host memory; the
- *               max_batch_segments field is ignored).
+ * through their own pool and allow no other allocator.  It computes the same autos,
+ * crosses and Stokes as create + feed + integrate_device for the whole segments of one
+ * input block (samples after the last whole segment are ignored; nothing is carried),
+ * but it keeps no handle: its scratch slab, accumulators, twiddles and window taps live
+ * in one static device array of 32 MiB (POLARIS_NOALLOC_BYTES), which every GPU that
+ * loads this library holds until the process exits.
+ *   cfg         as for spectrometer_create (the max_batch_segments and code_stats fields
+ *               are ignored).  Custom taps are host memory, copied in stream order:
+ *               pageable memory has been read when the call returns, pinned memory must
+ *               stay unchanged until the stream has passed this call.
  *   d_packed    n_if DEVICE pointers to the packed words; n_samples_per_if >= n_fft
  *               and a multiple of 32/bits.
+ *   params      as for spectrometer_integrate (NULL: linear feeds, psi = 0, unit gains).
  *   d_autos, d_cross, d_stokes  DEVICE outputs in the layouts of
  *               spectrometer_integrate (NULL skips one).
  * Work is queued on cuda_stream (NULL = legacy default stream); nothing is allocated
- * and nothing synchronises the host.  The first call on a device looks up the array's
- * device address (once per device, with that device made current); make that first
- * call before any stream capture.  Every call reuses the same array, which keeps the
- * previous call's contents (each call zeroes the accumulators it needs): calls whose
- * GPU work overlaps -- on different streams or devices' shared host threads -- race on
- * it and must be ordered by the caller.  A configuration whose accumulators, tables and
- * one segment of slab exceed 32 MiB is rejected with POLARIS_EINVAL and a message.
- * cfg->code_stats is ignored (no histogram is kept). */
+ * and nothing synchronises the host.  Every argument is checked before anything is
+ * queued: a call that returns POLARIS_EINVAL has queued no work and changed neither the
+ * array nor the outputs.  A configuration whose accumulators, tables and one segment of
+ * slab exceed 32 MiB is rejected that way, with a message.  The first call on a device
+ * looks up the array's device address (once per device, with that device made current).
+ * Every call reuses the same array, which keeps the previous call's contents (each call
+ * zeroes the accumulators it needs): calls on the same device whose GPU work overlaps
+ * (on different streams, say) race on the array and must be ordered by the caller.
+ * Because the call does not synchronise, a bounded device-side wait that ran out (see
+ * polaris_set_wait_limit) is not reported as a status: every output is then NaN. */
 int spectrometer_run_noalloc(const polaris_config* cfg, const void* const* d_packed, int64_t n_samples_per_if,
                              const polaris_stokes_params* params, float* d_autos, float* d_cross, float* d_stokes,
                              int64_t* n_segments_out, void* cuda_stream);
@@ -324,6 +348,18 @@ const char* polaris_tc_last_error(const polaris_tc* h);
  * Test hook: polls per wait for later launches (0 makes every such wait run out at once;
  * a negative value restores the default of 2^20). */
 void polaris_set_wait_limit(int64_t polls);
+
+/* Bounds-checked build.  Compiled with -DPOLARIS_CHECK, every kernel of the spectrometer
+ * path (phase kernels, readout, code histogram) tests each global-memory index that the
+ * hardware does not check (tensor-map copies are checked by the copy engine) against its
+ * buffer's extent; an index outside skips that access and sets the handle's device status
+ * word, and the next synchronising call returns POLARIS_EBOUNDS.  Nothing traps.
+ * polaris_checked_build: 1 in such a build, 0 otherwise.
+ * polaris_set_check_understate (test hook, checked build only): on != 0 makes later feeds
+ * tell the kernels half the slab they have, so that the checks fire while every access
+ * stays inside its buffer; POLARIS_EINVAL in a build without checks. */
+int polaris_checked_build(void);
+int polaris_set_check_understate(int on);
 
 /* Test hook: cap the bytes of device memory that later spectrometer_create
  * calls may allocate (-1 = no cap), so that allocation failure can be tested

@@ -82,6 +82,15 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False, o
     return LIB
 
 
+CHECKED_DIR = os.path.join(HERE, "_checked")
+
+
+def build_checked(force: bool = False) -> str:
+    """The bounds-checked variant (-DPOLARIS_CHECK) in paper_1412_1256_gb300/_checked/:
+    kernels test their global-memory indices and record a bad one instead of touching it."""
+    return build(force=force, out_dir=CHECKED_DIR, defines=("POLARIS_CHECK",))
+
+
 if __name__ == "__main__":
     import sys
 

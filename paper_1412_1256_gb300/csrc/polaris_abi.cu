@@ -3,6 +3,7 @@
 // (bit-exact checks) and the readout kernel that turns the integration accumulators
 // into autos, crosses and Stokes I, Q, U, V (Eq. 2).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstdarg>
@@ -43,7 +44,11 @@ POLARIS_DECLARE(20)
 typedef cudaError_t (*phase_fn)(const BatchArgs&, cudaStream_t, bool);
 // per-IF code histograms of segments [0, nseg) of `in` (polaris_stats.cu)
 cudaError_t launch_code_hist(const SegSrc& in, int n_if, int bits, int nseg, int64_t n_fft,
-                             unsigned long long* hist, int num_sms, cudaStream_t st);
+                             unsigned long long* hist, int* err, int num_sms, cudaStream_t st);
+// the staged data translation of phase 1 alone (polaris_debug.cu)
+bool phase1_staged(int logn, int bits);
+cudaError_t launch_unpack_staged(int logn, int bits, const uint32_t* pa, const uint32_t* pb, long long nseg, int dense,
+                                 float* oa, float* ob, cudaStream_t st);
 #define POLARIS_ROW(LOGN) {run_phase1<LOGN>, run_phase2<LOGN>}
 static const phase_fn kPhases[21][2] = {
     {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr}, {nullptr, nullptr},
@@ -86,6 +91,7 @@ struct ReadoutArgs {
   float c2, s2;
   float inv_ga2[kMaxIF], inv_gb2[kMaxIF], ig_re[kMaxIF], ig_im[kMaxIF];  // 1/|Ga|^2, 1/|Gb|^2, 1/(Ga conj Gb)
   const int* err;  // nonzero: a phase kernel gave up a wait; every output is NaN
+  long long acc_slots;  // accumulator slots over all copies (read by the checked build)
 };
 
 // Readout of one block: a tile of CT consecutive columns c times DT consecutive values of d,
@@ -127,6 +133,10 @@ __global__ void __launch_bounds__(kReadoutThreads) k_readout(ReadoutArgs a) {
     else if (c == N1 / 2) idx = (d <= N2 / 2 - 2) ? N2 / 2 + 1 + d : a.UPS * N2;
     else if (c < N1 / 2) idx = c * N2 + d;
     else idx = (N1 - c) * N2 + (N2 - 1 - d);
+    // (checked build: a slot outside the accumulators of every copy is recorded and skipped)
+    if (!in_bounds(const_cast<int*>(a.err), (long long)(a.copies > 1 ? a.copies - 1 : 0) * a.copy_stride + fo + idx,
+                   a.acc_slots))
+      continue;
     slot[i] = idx;
     sidx[i] = dd * (CT + 1) + cc;
     if (a.fp64) {
@@ -312,6 +322,13 @@ static int set_err(polaris_spec* s, int code, const char* fmt, ...) {
     if (e_ != cudaSuccess) return set_err((s), POLARIS_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
   } while (0)
 
+// NVTX range over one public call, so that a timeline profiler shows feed and integrate
+// (header-only NVTX 3: a no-op unless a tool is attached)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 struct DeviceGuard {
   int prev = -1;
   explicit DeviceGuard(int dev) {
@@ -392,6 +409,25 @@ static void free_all(polaris_spec* s) {
 }
 
 extern "C" void polaris_set_alloc_limit(int64_t bytes) { g_alloc_limit = bytes; }
+
+// test hook of the bounds-checked build: later feeds tell the kernels half the slab each pass uses
+static bool g_check_understate = false;
+extern "C" int polaris_set_check_understate(int on) {
+#ifdef POLARIS_CHECK
+  g_check_understate = on != 0;
+  return POLARIS_OK;
+#else
+  (void)on;
+  return POLARIS_EINVAL;
+#endif
+}
+extern "C" int polaris_checked_build(void) {
+#ifdef POLARIS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
+}
 
 // polls of a bounded device-side wait before it counts as timed out (test hook below)
 static constexpr unsigned kDefaultWaitLimit = 1u << 20;
@@ -623,6 +659,11 @@ static int check_device_status(polaris_spec* s) {
     s->broken = true;
     return set_err(s, POLARIS_ECUDA, "status read: %s", cudaGetErrorString(e));
   }
+  if (st == kErrBounds) {
+    set_err(s, POLARIS_EBOUNDS, "an index check of the bounds-checked build failed; outputs are NaN");
+    s->broken = true;
+    return POLARIS_EBOUNDS;
+  }
   if (st) {
     set_err(s, POLARIS_ETIMEOUT, "a device-side wait ran out of its bound; outputs are NaN");
     s->broken = true;
@@ -633,6 +674,7 @@ static int check_device_status(polaris_spec* s) {
 
 extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int64_t n, int on_device,
                                  void* cuda_stream) {
+  NvtxRange nvtx("polaris.feed");
   int rc = check_usable(s);
   if (rc) return rc;
   if (!packed) return set_err(s, POLARIS_EINVAL, "packed is NULL");
@@ -718,6 +760,8 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
   }
   a.in.hop_w = hop / spw;
   a.in.n0 = (int)n0;
+  a.in.in_words0 = s->stage_words_cap;
+  a.in.in_words1 = nw - (n0 * hop - carry) / spw;
   for (int f = 0; f < kMaxIF; ++f) {
     a.fa[f] = s->fa[f];
     a.fb[f] = s->fb[f];
@@ -733,10 +777,16 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
   a.num_sms = s->num_sms;
   a.err = s->d_err;
   a.wait_limit = g_wait_limit;
+  a.slab_elems = (long long)s->slab_half;
+  // (test hook: half of what the pass writes and reads)
+  auto understate = [&](BatchArgs& x) {
+    if (g_check_understate) x.slab_elems = (long long)x.nseg * s->n_fpair * s->N / 2;
+  };
+  a.acc_slots = (long long)s->acc_copies * s->n_fpair * s->native;
   const phase_fn f1 = kPhases[s->logn][0], f2 = kPhases[s->logn][1];
   if (nseg > 0 && s->code_stats) {
     cudaError_t e = counted_launch(s, 3, st, [&]() {
-      return launch_code_hist(a.in, s->n_if, s->bits, (int)nseg, N, s->d_hist, s->num_sms, st);
+      return launch_code_hist(a.in, s->n_if, s->bits, (int)nseg, N, s->d_hist, s->d_err, s->num_sms, st);
     });
     if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "code-histogram launch: %s", cudaGetErrorString(e));
   }
@@ -747,6 +797,7 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
     a.seg0 = 0;
     a.nseg = (int)nseg;
     a.scratch = s->d_scratch;
+    understate(a);
     const bool pdl = st != nullptr && !s->profiling;
     cudaError_t e = counted_launch(s, 0, st, [&]() { return f1(a, st, pdl); });
     if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "phase-1 launch: %s", cudaGetErrorString(e));
@@ -764,6 +815,7 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
       a.seg0 = (int)s0;
       a.nseg = (int)(nseg - s0 < s->max_batch ? nseg - s0 : s->max_batch);
       a.scratch = s->d_scratch + (size_t)(b & 1) * s->slab_half;
+      understate(a);
       // phase 1 of batch b may overwrite its slab half once phase 2 of batch b-2 has read it
       if (b >= 2) CUDA_OR_FAIL(s, cudaStreamWaitEvent(s->st_p1, s->ev_p2[b & 1], 0));
       cudaError_t e = counted_launch(s, 0, s->st_p1, [&]() { return f1(a, s->st_p1, false); });
@@ -806,6 +858,7 @@ static int fill_readout(polaris_spec* s, const polaris_stokes_params* prm, Reado
   r.copies = s->acc_copies;
   r.copy_stride = (long long)s->n_fpair * s->native;
   r.err = s->d_err;
+  r.acc_slots = (long long)s->acc_copies * s->n_fpair * s->native;
   r.fp64 = s->accum_fp64;
   r.N1 = s->N1;
   r.N2 = s->N2;
@@ -846,6 +899,7 @@ static int fill_readout(polaris_spec* s, const polaris_stokes_params* prm, Reado
 extern "C" int spectrometer_integrate_device(polaris_spec* s, const polaris_stokes_params* prm, float* d_autos,
                                              float* d_cross, float* d_stokes, int64_t* n_segments_out,
                                              void* cuda_stream) {
+  NvtxRange nvtx("polaris.integrate");
   int rc = check_usable(s);
   if (rc) return rc;
   if (s->seg_acc == 0) return set_err(s, POLARIS_ESTATE, "no segment accumulated since the last integrate");
@@ -943,6 +997,39 @@ extern "C" int spectrometer_debug_unpack(polaris_spec* s, const void* packed, in
   return POLARIS_OK;
 }
 
+extern "C" int spectrometer_debug_unpack_staged(polaris_spec* s, const void* packed_a, const void* packed_b, int64_t n,
+                                                int layout, float* out_a, float* out_b) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (!packed_a || !out_a || (packed_b && !out_b)) return set_err(s, POLARIS_EINVAL, "null pointer");
+  if (n <= 0 || n % s->N) return set_err(s, POLARIS_EINVAL, "n must be a positive multiple of n_fft");
+  if (layout != 0 && layout != 1) return set_err(s, POLARIS_EINVAL, "layout must be 0 (interleaved) or 1 (dense)");
+  if (!phase1_staged(s->logn, s->bits))
+    return set_err(s, POLARIS_EINVAL, "phase 1 does not stage its input at this size and width");
+  DeviceGuard dg(s->device);
+  const size_t nw = (size_t)(n / s->spw);
+  const int nif = packed_b ? 2 : 1;
+  uint32_t* dw = nullptr;
+  float* df = nullptr;
+  if (cudaMalloc((void**)&dw, nw * 4 * nif) != cudaSuccess || cudaMalloc((void**)&df, (size_t)n * 4 * nif) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(dw);
+    cudaFree(df);
+    return set_err(s, POLARIS_ENOMEM, "debug_unpack_staged allocation failed");
+  }
+  cudaError_t e = cudaMemcpy(dw, packed_a, nw * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && packed_b) e = cudaMemcpy(dw + nw, packed_b, nw * 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = launch_unpack_staged(s->logn, s->bits, dw, packed_b ? dw + nw : nullptr, (long long)(n / s->N), layout, df,
+                             packed_b ? df + n : nullptr, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(out_a, df, (size_t)n * 4, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && packed_b) e = cudaMemcpy(out_b, df + n, (size_t)n * 4, cudaMemcpyDeviceToHost);
+  cudaFree(dw);
+  cudaFree(df);
+  if (e != cudaSuccess) return set_err(s, POLARIS_ECUDA, "debug_unpack_staged: %s", cudaGetErrorString(e));
+  return POLARIS_OK;
+}
+
 extern "C" int64_t spectrometer_kernel_launches(const polaris_spec* s) { return s ? s->launches : -1; }
 
 extern "C" int spectrometer_set_profiling(polaris_spec* s, int on) {
@@ -994,13 +1081,14 @@ extern "C" int spectrometer_code_histogram(polaris_spec* s, uint64_t* counts, in
 // Allocation-free one-shot variant.
 //
 // Some callers cannot allocate device memory at the point where they need a spectrum:
-// code running while a CUDA graph is being captured (cudaMalloc is not capturable),
-// real-time loops where cudaMalloc/cudaFree would synchronise the device and miss a
+// real-time loops in which cudaMalloc/cudaFree would synchronise the device and miss a
 // sampler deadline, and host frameworks that own all device memory through their own
 // pool and forbid other allocators.  For them spectrometer_run_noalloc computes one
 // integration without a handle: its scratch slab, accumulators, twiddle table and
 // window taps live in the file-scope array below, which every GPU that loads this
-// library holds until the process exits.
+// library holds until the process exits.  Every argument is checked before the first
+// operation is queued.  The call never synchronises, so a bounded device-side wait that
+// ran out is not reported as a status: it shows as NaN in every output.
 // =======================================================================================
 #define POLARIS_NOALLOC_BYTES (32u << 20)
 static __device__ __align__(256) unsigned char g_noalloc_scratch[POLARIS_NOALLOC_BYTES];
@@ -1034,6 +1122,7 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
                                         int64_t n_samples_per_if, const polaris_stokes_params* prm, float* d_autos,
                                         float* d_cross, float* d_stokes, int64_t* n_segments_out,
                                         void* cuda_stream) {
+  NvtxRange nvtx("polaris.run_noalloc");
   if (!cfg || !d_packed) return set_err(nullptr, POLARIS_EINVAL, "null config or input");
   const polaris_config& c = *cfg;
   if (c.n_if < 1 || c.n_if > kMaxIF) return set_err(nullptr, POLARIS_EINVAL, "n_if must be in [1, %d]", kMaxIF);
@@ -1095,6 +1184,29 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
     fcorr[nf++] = -1;
   }
   for (int f = nf; f < kMaxIF; ++f) fa[f] = fb[f] = fcorr[f] = -1;
+  // Stokes parameters (checked here, before anything is queued: a rejected call leaves the
+  // static array and the outputs untouched)
+  const int feed = prm ? prm->feed : POLARIS_FEED_LINEAR;
+  if (feed != POLARIS_FEED_LINEAR && feed != POLARIS_FEED_CIRCULAR) return set_err(nullptr, POLARIS_EINVAL, "bad feed");
+  const double psi = prm ? prm->psi_m : 0.0;
+  const float c2 = (float)std::cos(2.0 * psi), s2 = (float)std::sin(2.0 * psi);
+  float inv_ga2[kMaxIF], inv_gb2[kMaxIF], ig_re[kMaxIF], ig_im[kMaxIF];
+  for (int p = 0; p < n_pair; ++p) {
+    double gar = 1, gai = 0, gbr = 1, gbi = 0;
+    if (prm && prm->gains) {
+      gar = prm->gains[4 * p + 0];
+      gai = prm->gains[4 * p + 1];
+      gbr = prm->gains[4 * p + 2];
+      gbi = prm->gains[4 * p + 3];
+    }
+    const double gaa = gar * gar + gai * gai, gbb = gbr * gbr + gbi * gbi;
+    if (gaa == 0.0 || gbb == 0.0) return set_err(nullptr, POLARIS_EINVAL, "zero gain for pair %d", p);
+    const double gr = gar * gbr + gai * gbi, gi = gai * gbr - gar * gbi, g2 = gr * gr + gi * gi;
+    inv_ga2[p] = (float)(1.0 / gaa);
+    inv_gb2[p] = (float)(1.0 / gbb);
+    ig_re[p] = (float)(gr / g2);
+    ig_im[p] = (float)(-gi / g2);
+  }
   int logn = 0;
   while ((1LL << logn) < N) ++logn;
   const int N2 = host_plan_n2(logn), N1 = (int)(N / N2), UPS = N1 / 2, native = UPS * N2 + 1;
@@ -1159,6 +1271,7 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
   }
   a.in.hop_w = hop / spw;
   a.in.n0 = 0;
+  a.in.in_words0 = a.in.in_words1 = n_samples_per_if / spw;
   for (int f = 0; f < kMaxIF; ++f) {
     a.fa[f] = fa[f];
     a.fb[f] = fb[f];
@@ -1171,6 +1284,8 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
   a.tw = tw;
   a.acc = acc;
   a.acc_copies = 1;
+  a.slab_elems = (long long)batch * nf * N;
+  a.acc_slots = (long long)nf * native;
   a.fp64 = c.accum_fp64 ? 1 : 0;
   a.bits = c.bits;
   a.num_sms = num_sms;
@@ -1187,6 +1302,7 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
   r.copies = 1;
   r.copy_stride = (long long)nf * native;
   r.err = d_err;
+  r.acc_slots = (long long)nf * native;
   r.fp64 = a.fp64;
   r.N1 = N1;
   r.N2 = N2;
@@ -1198,27 +1314,14 @@ extern "C" int spectrometer_run_noalloc(const polaris_config* cfg, const void* c
     r.fb[f] = fb[f];
     r.fcorr[f] = fcorr[f];
   }
-  const int feed = prm ? prm->feed : POLARIS_FEED_LINEAR;
-  if (feed != POLARIS_FEED_LINEAR && feed != POLARIS_FEED_CIRCULAR) return set_err(nullptr, POLARIS_EINVAL, "bad feed");
-  const double psi = prm ? prm->psi_m : 0.0;
   r.feed = feed;
-  r.c2 = (float)std::cos(2.0 * psi);
-  r.s2 = (float)std::sin(2.0 * psi);
+  r.c2 = c2;
+  r.s2 = s2;
   for (int p = 0; p < n_pair; ++p) {
-    double gar = 1, gai = 0, gbr = 1, gbi = 0;
-    if (prm && prm->gains) {
-      gar = prm->gains[4 * p + 0];
-      gai = prm->gains[4 * p + 1];
-      gbr = prm->gains[4 * p + 2];
-      gbi = prm->gains[4 * p + 3];
-    }
-    const double gaa = gar * gar + gai * gai, gbb = gbr * gbr + gbi * gbi;
-    if (gaa == 0.0 || gbb == 0.0) return set_err(nullptr, POLARIS_EINVAL, "zero gain for pair %d", p);
-    const double gr = gar * gbr + gai * gbi, gi = gai * gbr - gar * gbi, g2 = gr * gr + gi * gi;
-    r.inv_ga2[p] = (float)(1.0 / gaa);
-    r.inv_gb2[p] = (float)(1.0 / gbb);
-    r.ig_re[p] = (float)(gr / g2);
-    r.ig_im[p] = (float)(-gi / g2);
+    r.inv_ga2[p] = inv_ga2[p];
+    r.inv_gb2[p] = inv_gb2[p];
+    r.ig_re[p] = ig_re[p];
+    r.ig_im[p] = ig_im[p];
   }
   r.autos = d_autos;
   r.cross = n_pair ? d_cross : nullptr;

@@ -62,6 +62,7 @@ struct SegSrc {
   const uint32_t* src1[kMaxIF];
   long long hop_w;  // 32-bit words between segment starts
   int n0;
+  long long in_words0, in_words1;  // words reachable from src0 / src1 (read by the checked build)
 };
 
 struct BatchArgs {
@@ -81,7 +82,30 @@ struct BatchArgs {
   int num_sms;
   int* err;             // device status word: set to 1 when a bounded wait ran out (see k_phase2)
   unsigned wait_limit;  // iterations of a bounded mbarrier wait before it counts as timed out
+  // buffer extents, read only by the bounds-checked build (POLARIS_CHECK): float2 elements of
+  // this pass's slab, accumulator slots (float4 or double4) over all copies
+  long long slab_elems, acc_slots;
 };
+
+// Bounds-checked build (-DPOLARIS_CHECK): every global-memory index of the hot-path kernels
+// that is not checked by the hardware (tensor-map copies are) is tested against its buffer's
+// extent; an index outside sets the device status word to kErrBounds and the access is
+// skipped (a load gives zero).  Nothing traps.  In the normal build the test is compiled out.
+constexpr int kErrBounds = 2;
+#ifdef POLARIS_CHECK
+__device__ __forceinline__ bool in_bounds(int* err, long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  if (err) atomicExch(err, kErrBounds);
+  return false;
+}
+#else
+__device__ __forceinline__ constexpr bool in_bounds(int*, long long, long long) { return true; }
+#endif
+// word offset of segment s's first word from the start of its source (src0 or src1), and
+// that source's extent
+__device__ __forceinline__ long long seg_word0(const SegSrc& in, int s) {
+  return s < in.n0 ? (long long)s * in.hop_w : (long long)(s - in.n0) * in.hop_w;
+}
 
 // Tensor maps of the packed input for phase 1's TMA staging: m[0][i] views IF i's staged
 // segments [0, n0) and m[1][i] its segments from n0 on, each as words x rows x segments.
@@ -226,6 +250,7 @@ __device__ __forceinline__ void p1_load(const BatchArgs& a, int g, int b, int q1
   const int ia = a.fa[f], ib = a.fb[f];
   const uint32_t* pa = seg_ptr(a.in, ia, s);
   const uint32_t* pb = ib >= 0 ? seg_ptr(a.in, ib, s) : nullptr;
+  const long long w0 = seg_word0(a.in, s), wext = s < a.in.n0 ? a.in.in_words0 : a.in.in_words1;
   const float* taps = a.taps;
   const uint32_t base = (uint32_t)(N2 * q1 + b);  // sample index of t = 0 within the segment
   sfor<0, P>([&](auto t_) {
@@ -239,8 +264,9 @@ __device__ __forceinline__ void p1_load(const BatchArgs& a, int g, int b, int q1
       word_i = (n * BITS) >> 5;
       shift = (n * BITS) & 31u;
     }
-    float x = decode_level<BITS>(__ldg(pa + word_i), shift);
-    float y = pb ? decode_level<BITS>(__ldg(pb + word_i), shift) : 0.0f;
+    const bool ok = in_bounds(a.err, w0 + word_i, wext);
+    float x = decode_level<BITS>(ok ? __ldg(pa + word_i) : 0u, shift);
+    float y = pb ? decode_level<BITS>(ok ? __ldg(pb + word_i) : 0u, shift) : 0.0f;
     if (taps) {
       const float wv = __ldg(taps + n);
       x *= wv;
@@ -248,6 +274,35 @@ __device__ __forceinline__ void p1_load(const BatchArgs& a, int g, int b, int q1
     }
     v[ct::bitrev(t, P)] = make_float2(x, y);
   });
+}
+
+// Data translation of the staged phase 1 (N >= 2^13), shared with the bit-exactness check
+// (k_unpack_staged): column `col` of a tile starts at word p1_col_word(col) of each staged row,
+// and its code sits at rotation p1_col_rot(col) of that word.
+template <int BITS>
+__device__ __forceinline__ int p1_col_word(int col) { return (col * BITS) >> 5; }
+template <int BITS>
+__device__ __forceinline__ uint32_t p1_col_rot(int col) { return decode_rot<BITS>((uint32_t)((col * BITS) & 31)); }
+// The codes of staged row `row` at word wd, decoded at rotation rot, before the window:
+// (level of IF a, level of IF b) for a pair with an IF b (HB), else (level of IF a, 0).
+// Interleaved stage (cp.async, TL false): word w of IF a at 2w, of IF b at 2w + 1 of the
+// row's RS words.  Dense stage (TMA, TL true): [IF][row][WPR].
+template <int BITS, bool TL, bool HB, int N1, int WPR, int RS>
+__device__ __forceinline__ float2 p1_stage_decode(const uint32_t* sb, int row, int wd, uint32_t rot) {
+  uint32_t wa, wb = 0;
+  if constexpr (TL) {
+    wa = sb[row * WPR + wd];
+    if constexpr (HB) wb = sb[N1 * WPR + row * WPR + wd];
+  } else {
+    const uint2 w = *reinterpret_cast<const uint2*>(sb + row * RS + 2 * wd);  // IF a, IF b
+    wa = w.x;
+    wb = w.y;
+  }
+  if constexpr (HB) {
+    return decode_pair_rot<BITS>(wa, wb, rot);
+  } else {
+    return make_float2(decode_level_rot<BITS>(wa, rot), 0.0f);
+  }
 }
 
 __device__ __forceinline__ void corr_acc(float (&acc)[4], float2 U, float2 V) {
@@ -453,7 +508,8 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
             float2* dst = a.scratch + ((size_t)g * N1 + p) * N2 + b;
             sfor<0, Q1>([&](auto m_) {
               constexpr int m = decltype(m_)::value;
-              dst[(size_t)m * P * N2] = u[m];
+              if (in_bounds(a.err, ((long long)g * N1 + p + (long long)m * P) * N2 + b, a.slab_elems))
+                dst[(size_t)m * P * N2] = u[m];
             });
           }
         });
@@ -464,7 +520,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
         float2* dst = a.scratch + (size_t)g * N1 * N2 + b;
         sfor<0, P>([&](auto p_) {
           constexpr int p = decltype(p_)::value;
-          dst[(size_t)p * N2] = v[p];
+          if (in_bounds(a.err, (long long)g * N1 * N2 + (long long)p * N2 + b, a.slab_elems)) dst[(size_t)p * N2] = v[p];
         });
       }
     }
@@ -516,11 +572,15 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
       const uint32_t* pa = seg_ptr(a.in, ia, sg) + (b0 * BITS) / 32;
       const uint32_t* pb = ib >= 0 ? seg_ptr(a.in, ib, sg) + (b0 * BITS) / 32 : pa;
       const uint32_t dst0 = stage_a + 4u * (uint32_t)(buf * SB);
+      const long long w0 = seg_word0(a.in, sg) + (b0 * BITS) / 32;
+      const long long wext = sg < a.in.n0 ? a.in.in_words0 : a.in.in_words1;
       sfor<0, KPT>([&](auto i_) {
         constexpr int i = decltype(i_)::value;
         if (KW % PL::THREADS == 0 || (int)threadIdx.x + i * PL::THREADS < KW) {
-          cp_async4(dst0 + doff[i], pa + soff[i]);
-          cp_async4(dst0 + doff[i] + 4u, pb + soff[i]);  // (IF a again when the pair has no IF b)
+          if (in_bounds(a.err, w0 + soff[i], wext)) {
+            cp_async4(dst0 + doff[i], pa + soff[i]);
+            cp_async4(dst0 + doff[i] + 4u, pb + soff[i]);  // (IF a again when the pair has no IF b)
+          }
         }
       });
       cp_async_commit();
@@ -612,33 +672,18 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
       for (int it = it_begin; it < it_end; ++it) {
         const int col = (it * PL::WARPS + warp) * CW + cw;  // column inside the tile
         const long long b = b0 + col;
-        const int wd = (col * BITS) >> 5;
-        const uint32_t rot = decode_rot<BITS>((uint32_t)((col * BITS) & 31));
+        const int wd = p1_col_word<BITS>(col);
+        const uint32_t rot = p1_col_rot<BITS>(col);
         const uint32_t* sb = stage + buf * SB;
         float2 v[P];
-        // decode the lane's rows; the stage layout, the pair's shape and the window are
-        // uniform per tile.  Interleaved layout (cp.async): word w of IF a at 2w, of IF b
-        // at 2w + 1 of row r's RS words.  Dense layout (TMA): [IF][row][WPR].
+        // decode the lane's rows; the stage layout (TL), the pair's shape (HB) and the
+        // window (TP) are uniform per tile
         auto decode = [&](auto tl_, auto hb_, auto tp_) {
           constexpr bool TL = decltype(tl_)::value, HB = decltype(hb_)::value, TP = decltype(tp_)::value;
           sfor<0, P>([&](auto t_) {
             constexpr int t = decltype(t_)::value;
             const int row = q1 + Q1 * t;
-            uint32_t wa, wb = 0;
-            if constexpr (TL) {
-              wa = sb[row * WPR + wd];
-              if constexpr (HB) wb = sb[N1 * WPR + row * WPR + wd];
-            } else {
-              const uint2 w = *reinterpret_cast<const uint2*>(sb + row * RS + 2 * wd);  // IF a, IF b
-              wa = w.x;
-              wb = w.y;
-            }
-            float2 z;
-            if constexpr (HB) {
-              z = decode_pair_rot<BITS>(wa, wb, rot);
-            } else {
-              z = make_float2(decode_level_rot<BITS>(wa, rot), 0.0f);
-            }
+            float2 z = p1_stage_decode<BITS, TL, HB, N1, WPR, RS>(sb, row, wd, rot);
             if constexpr (TP) {
               const float tv = __ldg(a.taps + row * N2 + b);
               z.x *= tv;
@@ -715,12 +760,17 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
   bool stop = false;  // a bounded wait ran out: no further work, no flush
   // the columns of units ug_ UPW .. ug_ UPW + UPW - 1 of segment s_ of FFT pair f_: unit w's
   // column c and mirror N1 - c (0 and N1/2 for unit 0) at region columns 2w, 2w + 1
+  // column c_ of segment s_ of pair f_; in the checked build an out-of-range column is recorded
+  // and read from the slab's start instead (the barrier still receives its bytes)
+  auto colp = [&](int f_, int s_, int c_) -> const float2* {
+    const long long o = (((long long)s_ * a.n_fpair + f_) * N1 + c_) * N2;
+    return a.scratch + (in_bounds(a.err, o + N2 - 1, a.slab_elems) ? o : 0);
+  };
   auto prefetch = [&](int f_, int ug_, int s_) {
-    const float2* col = a.scratch + ((size_t)s_ * a.n_fpair + f_) * N1 * N2;
     if constexpr (UPW == 1) {
       const int u_ = ug_;
       const int c0 = (u_ == 0) ? 0 : u_, c1 = (u_ == 0) ? N1 / 2 : N1 - u_;
-      bulk_load2_elect(bar, smem_addr(region), col + (size_t)c0 * N2, smem_addr(region + N2), col + (size_t)c1 * N2,
+      bulk_load2_elect(bar, smem_addr(region), colp(f_, s_, c0), smem_addr(region + N2), colp(f_, s_, c1),
                        (uint32_t)(N2 * sizeof(float2)));
     } else {
       if (lane == 0) {
@@ -730,8 +780,8 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
           constexpr int w = decltype(w_)::value;
           const int u_ = ug_ * UPW + w;
           const int c0 = (u_ == 0) ? 0 : u_, c1 = (u_ == 0) ? N1 / 2 : N1 - u_;
-          bulk_load(bar, smem_addr(region + (2 * w) * (N2 + PL::PADC)), col + (size_t)c0 * N2, bytes);
-          bulk_load(bar, smem_addr(region + (2 * w + 1) * (N2 + PL::PADC)), col + (size_t)c1 * N2, bytes);
+          bulk_load(bar, smem_addr(region + (2 * w) * (N2 + PL::PADC)), colp(f_, s_, c0), bytes);
+          bulk_load(bar, smem_addr(region + (2 * w + 1) * (N2 + PL::PADC)), colp(f_, s_, c1), bytes);
         });
       }
       __syncwarp();
@@ -830,10 +880,12 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
         });
         __syncwarp();  // every lane has its column before the transpose overwrites the region
       } else {
-        const float2* src = a.scratch + ((size_t)(act ? s : 0) * a.n_fpair + f) * N1 * N2 + (size_t)c * N2 + q2;
+        const long long so = ((long long)(act ? s : 0) * a.n_fpair + f) * N1 * N2 + (long long)c * N2 + q2;
+        const float2* src = a.scratch + so;
         sfor<0, P>([&](auto t_) {
           constexpr int t = decltype(t_)::value;
-          v[ct::bitrev(t, P)] = act ? __ldcg(src + Q2 * t) : make_float2(0.f, 0.f);
+          v[ct::bitrev(t, P)] = (act && in_bounds(a.err, so + Q2 * t, a.slab_elems)) ? __ldcg(src + Q2 * t)
+                                                                                       : make_float2(0.f, 0.f);
         });
       }
       sfor<0, (P + 7) / 8>([&](auto c_) {
@@ -960,7 +1012,8 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
             const int d = j * PP + r + P * m;
             const float* q = a16 + 4 * (slot - 4 * cc);
             const size_t o = base + (size_t)u * N2 + d;
-            if (!a.fp64) {
+            if (!in_bounds(a.err, (long long)o, a.acc_slots)) {
+            } else if (!a.fp64) {
               atomicAdd(reinterpret_cast<float4*>(a.acc) + o, make_float4(q[0], q[1], q[2], q[3]));
             } else {
               double* op = reinterpret_cast<double*>(a.acc) + 4 * o;
@@ -973,7 +1026,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
         });
       }
     });
-    if (worked && special && j == 0) {
+    if (worked && special && j == 0 && in_bounds(a.err, (long long)(base + (size_t)UPS * N2), a.acc_slots)) {
       const size_t o = base + (size_t)UPS * N2;
       if (!a.fp64) {
         atomicAdd(reinterpret_cast<float4*>(a.acc) + o, make_float4(extra[0], extra[1], extra[2], extra[3]));

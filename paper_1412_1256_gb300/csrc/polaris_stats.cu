@@ -16,6 +16,7 @@ struct HistArgs {
   int nseg;                  // segments [0, nseg) of `in`
   int wps_log2;              // log2 of the 32-bit words per segment (N * bits / 32)
   unsigned long long* hist;  // [n_if][2^bits], accumulated with atomics
+  int* err;                  // status word (the bounds-checked build records a bad index)
 };
 
 // counts of each code value in one 32-bit word (codes are the word's bits / BITS fields)
@@ -81,7 +82,9 @@ __global__ void __launch_bounds__(kHistThreads, 2) k_code_hist(HistArgs a) {
       w[j] = 0;
       if (k < total) {
         const int s = (int)(k >> a.wps_log2);
-        w[j] = __ldg((s < n0 ? src0 + s * hop_w : src1 + (s - n0) * hop_w) + (k & wmask));
+        const long long o = (s < n0 ? s * hop_w : (s - n0) * hop_w) + (k & wmask);
+        if (in_bounds(a.err, o, s < n0 ? a.in.in_words0 : a.in.in_words1))
+          w[j] = __ldg((s < n0 ? src0 : src1) + o);
       }
     }
 #pragma unroll
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(kHistThreads, 2) k_code_hist(HistArgs a) {
 }
 
 cudaError_t launch_code_hist(const SegSrc& in, int n_if, int bits, int nseg, int64_t n_fft,
-                             unsigned long long* hist, int num_sms, cudaStream_t st) {
+                             unsigned long long* hist, int* err, int num_sms, cudaStream_t st) {
   if (nseg <= 0) return cudaSuccess;
   int wl = 0;
   while ((1LL << wl) < n_fft * bits / 32) ++wl;
@@ -121,6 +124,7 @@ cudaError_t launch_code_hist(const SegSrc& in, int n_if, int bits, int nseg, int
   a.nseg = nseg;
   a.wps_log2 = wl;
   a.hist = hist;
+  a.err = err;
   const long long total = (long long)nseg << wl;
   const long long chunk = (long long)kHistThreads * kHistWords;
   long long bx = (total + chunk - 1) / chunk;                 // one pass per block where possible

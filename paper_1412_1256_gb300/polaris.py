@@ -18,20 +18,21 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 # POLARIS_LIB selects another build of the library (e.g. a tuning variant)
 LIB_PATH = os.environ.get("POLARIS_LIB") or os.path.join(HERE, "libpolaris.so")
 
-OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT = 0, -1, -2, -3, -4, -5
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, EBOUNDS = 0, -1, -2, -3, -4, -5, -6
 WIN_RECT, WIN_HANN, WIN_CUSTOM = 0, 1, 2
 FEED_LINEAR, FEED_CIRCULAR = 0, 1
 TC_BF16X3, TC_FP16X3, TC_BF16X1 = 0, 1, 2
 INPUT_HOST, INPUT_DEVICE, INPUT_HOST_ASYNC = 0, 1, 2
-STATUS_NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ESTATE: "ESTATE", ETIMEOUT: "ETIMEOUT"}
+STATUS_NAMES = {EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA", ESTATE: "ESTATE", ETIMEOUT: "ETIMEOUT",
+                EBOUNDS: "EBOUNDS"}
 
 EXPORTS = (
     "spectrometer_create", "spectrometer_feed", "spectrometer_integrate", "spectrometer_integrate_device",
     "spectrometer_n_bins", "spectrometer_n_pairs", "spectrometer_debug_unpack", "spectrometer_destroy",
-    "spectrometer_last_error", "polaris_set_alloc_limit", "spectrometer_kernel_launches",
+    "spectrometer_last_error", "spectrometer_debug_unpack_staged", "polaris_set_alloc_limit", "spectrometer_kernel_launches",
     "spectrometer_set_profiling", "spectrometer_kernel_times", "spectrometer_run_noalloc",
     "spectrometer_code_histogram", "polaris_power_from_histogram", "polaris_set_wait_limit",
-    "spectrometer_integrate_async",
+    "spectrometer_integrate_async", "polaris_checked_build", "polaris_set_check_understate",
     "polaris_adj_create", "polaris_adj_run", "polaris_adj_destroy", "polaris_adj_last_error",
     "polaris_tc_create", "polaris_tc_feed", "polaris_tc_integrate", "polaris_tc_set_wait_limit",
     "polaris_tc_destroy", "polaris_tc_last_error",
@@ -89,6 +90,8 @@ def load(path: str = LIB_PATH):
             lib.spectrometer_n_pairs.restype = ci
             lib.spectrometer_debug_unpack.argtypes = [vp, vp, i64, vp]
             lib.spectrometer_debug_unpack.restype = ci
+            lib.spectrometer_debug_unpack_staged.argtypes = [vp, vp, vp, i64, ci, vp, vp]
+            lib.spectrometer_debug_unpack_staged.restype = ci
             lib.spectrometer_destroy.argtypes = [vp]
             lib.spectrometer_destroy.restype = None
             lib.spectrometer_last_error.argtypes = [vp]
@@ -105,6 +108,10 @@ def load(path: str = LIB_PATH):
             lib.spectrometer_run_noalloc.restype = ci
             lib.polaris_set_alloc_limit.argtypes = [i64]
             lib.polaris_set_alloc_limit.restype = None
+            lib.polaris_checked_build.argtypes = []
+            lib.polaris_checked_build.restype = ci
+            lib.polaris_set_check_understate.argtypes = [ci]
+            lib.polaris_set_check_understate.restype = ci
             lib.polaris_adj_create.argtypes = [i64, ci, ci, ctypes.POINTER(vp)]
             lib.polaris_adj_create.restype = ci
             lib.polaris_adj_run.argtypes = [vp, ctypes.POINTER(vp), i64] + [vp] * 10
@@ -341,6 +348,20 @@ class Spectrometer:
         self._check(load().spectrometer_debug_unpack(self._h, w.ctypes.data, int(n), out.ctypes.data))
         return out[:n]
 
+    def debug_unpack_staged(self, words_a: np.ndarray, words_b, n: int, layout: int = 0):
+        """Levels of n samples (whole segments) of IF a and IF b (words_b None: a pair without
+        an IF b) through the FFT kernel's staged decoder; layout 0 interleaved, 1 dense.
+        Returns (levels_a, levels_b or None)."""
+        wa = np.ascontiguousarray(words_a, dtype=np.uint32)
+        wb = None if words_b is None else np.ascontiguousarray(words_b, dtype=np.uint32)
+        oa = np.empty(n, np.float32)
+        ob = None if wb is None else np.empty(n, np.float32)
+        self._check(load().spectrometer_debug_unpack_staged(self._h, wa.ctypes.data,
+                                                            None if wb is None else wb.ctypes.data, int(n),
+                                                            int(layout), oa.ctypes.data,
+                                                            None if ob is None else ob.ctypes.data))
+        return oa, ob
+
 
 def run_noalloc(packed, n_samples: int, bits: int, n_fft: int, autos, cross, stokes, hop: int = 0, window="rect",
                 pairs=None, accum_fp64: bool = False, device: int = 0, feed: int = FEED_LINEAR, psi: float = 0.0,
@@ -348,7 +369,8 @@ def run_noalloc(packed, n_samples: int, bits: int, n_fft: int, autos, cross, sto
     """spectrometer_run_noalloc: one integration of device-resident packed streams into
     device output tensors, using only the library's static device array (no allocation
     by the library).  For callers that cannot allocate device memory at this point, e.g.
-    while a CUDA graph is captured or inside a real-time loop.  Returns the segment count."""
+    a real-time loop that must not synchronise the device, or a host that owns all device
+    memory.  Returns the segment count."""
     lib = load()
     cfg = polaris_config()
     cfg.n_if, cfg.bits, cfg.n_fft, cfg.hop = len(packed), bits, n_fft, hop

@@ -28,3 +28,12 @@ def test_library_exports_every_declared_symbol():
     for name in _declared():
         assert hasattr(lib, name), name
     assert set(polaris.EXPORTS) == set(_declared())
+
+
+def test_normal_build_has_no_bounds_checks():
+    """The default library is built without -DPOLARIS_CHECK: its check hook refuses."""
+    from paper_1412_1256_gb300 import polaris
+
+    lib = polaris.load()
+    assert lib.polaris_checked_build() == 0
+    assert lib.polaris_set_check_understate(1) == polaris.EINVAL

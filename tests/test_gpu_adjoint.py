@@ -1,12 +1,58 @@
 """GPU parity of the leakage-calibration model and its adjoint (polaris_adj_*): Stokes and
 loss against the FP64 oracle, gradients against the oracle's FP64 gradient (itself pinned by
-central differences), and the torch.autograd wrapper against the direct call."""
+central differences) element by element and against central differences of the FP64 oracle
+loss, and the torch.autograd wrapper against the direct call.
+
+Gradient bound, per element: |g - g_ref| <= 1e-3 |g_ref| + 1e-6 max|g_ref| (max over the
+gradient's family: window taps, gains or leakage terms).  The relative part is the 1e-3 the
+calibration asks for; the floor covers elements that nearly cancel.  An FP32 transform of
+log2 N <= 14 radix-2 stages carries a relative error of about log2 N * 2^-24 ~ 1e-6 per term
+(the measured median relative error of the gradients is 3e-7..1.5e-6), and an element that
+cancels sums terms no larger than its family's largest element, so its absolute error is
+about 1e-6 of that maximum (measured: at most 2.7e-7 of it)."""
 import numpy as np
 import pytest
 
 from paper_1412_1256_gb300 import synth
 
 pytestmark = pytest.mark.gpu
+REL, FLOOR = 1e-3, 1e-6
+
+
+def _assert_grad(got, ref, what):
+    got = np.asarray(got, np.float64).reshape(-1)
+    ref = np.asarray(ref, np.float64).reshape(-1)
+    bound = REL * np.abs(ref) + FLOOR * np.abs(ref).max()
+    bad = np.abs(got - ref) > bound
+    assert not bad.any(), (what, int(bad.sum()), float(np.max(np.abs(got - ref) / bound)))
+
+
+def _fd_checks(orc, host, bits, n_fft, n, w, g, d, target, r, taps, leaks, h=1e-3):
+    """The GPU gradient against central differences (step h) of the FP64 oracle loss, for the
+    four gain components, the given window taps and the given leakage terms, within 1e-3
+    relative.  The loss is a quartic polynomial in each parameter, so the truncation error
+    h^2 f'''/6 stays far below that."""
+    w64, g64, d64 = (np.asarray(x, np.float64) for x in (w, g, d))
+
+    def L(w_, g_, d_):
+        return orc.leak_forward(host, bits, n_fft, n, w_, g_, d_, target)[1]
+
+    ggr, gwr, gdr = (r[k].cpu().numpy().astype(np.float64) for k in ("grad_gains", "grad_window", "grad_leak"))
+    for i in range(4):
+        e = np.zeros(4)
+        e[i] = h
+        fd = (L(w64, g64 + e, d64) - L(w64, g64 - e, d64)) / (2 * h)
+        assert ggr[i] == pytest.approx(fd, rel=REL), ("gain", i)
+    for i in taps:
+        e = np.zeros(n_fft)
+        e[i] = h
+        fd = (L(w64 + e, g64, d64) - L(w64 - e, g64, d64)) / (2 * h)
+        assert gwr[i] == pytest.approx(fd, rel=REL), ("tap", i)
+    for (f, k, c) in leaks:
+        e = np.zeros_like(d64)
+        e[f, k, c] = h
+        fd = (L(w64, g64, d64 + e) - L(w64, g64, d64 - e)) / (2 * h)
+        assert gdr[f, k, c] == pytest.approx(fd, rel=REL), ("leak", f, k, c)
 
 
 @pytest.fixture(scope="module")
@@ -59,9 +105,9 @@ def test_forward_and_gradients_match_oracle(env, orc, logn, bits, nseg):
     scale = np.abs(st_ref).max()
     assert np.abs(st - st_ref).max() <= 1e-5 * scale
     assert float(r["loss"].cpu()[0]) == pytest.approx(loss_ref, rel=1e-3)
-    for got, ref in ((r["grad_window"], gw_ref), (r["grad_gains"], gg_ref), (r["grad_leak"], gd_ref)):
-        got = got.cpu().numpy().astype(np.float64)
-        assert np.abs(got - ref).max() <= 2e-3 * np.abs(ref).max()
+    for name, got, ref in (("window", r["grad_window"], gw_ref), ("gains", r["grad_gains"], gg_ref),
+                           ("leak", r["grad_leak"], gd_ref)):
+        _assert_grad(got.cpu().numpy(), ref, name)
 
 
 def test_autograd_wrapper_matches_direct_call(env):
@@ -129,45 +175,31 @@ def test_full_size_circular_source_against_oracle(env, orc):
     st = r["stokes"].cpu().numpy()
     assert np.abs(st - st_ref).max() <= 1e-5 * np.abs(st_ref).max()
     assert float(r["loss"].cpu()[0]) == pytest.approx(loss_ref, rel=1e-3)
-    for got, ref in ((r["grad_window"], gw_ref), (r["grad_gains"], gg_ref), (r["grad_leak"], gd_ref)):
-        got = got.cpu().numpy().astype(np.float64)
-        assert np.abs(got - ref).max() <= 2e-3 * np.abs(ref).max()
+    for name, got, ref in (("window", r["grad_window"], gw_ref), ("gains", r["grad_gains"], gg_ref),
+                           ("leak", r["grad_leak"], gd_ref)):
+        _assert_grad(got.cpu().numpy(), ref, name)
+    nb = n_fft // 2 + 1
+    _fd_checks(orc, packed, 8, n_fft, n, w, g, d, target, r, taps=(3, 8191, 12371),
+               leaks=[(0, 3, 0), (1, nb // 3, 1), (0, nb - 1, 0)])
 
 
-def test_gradients_match_central_differences_on_gpu(env):
-    """d loss / d parameter from the adjoint against central differences of the library's
-    own loss: h = 1e-3 for gains and leakage, h = 1e-2 for window taps (a tap moves the
-    loss by ~1/N of itself, so a smaller step drowns in fp32 rounding of the transform)."""
+@pytest.mark.parametrize("logn,bits,nseg", [(6, 8, 6), (8, 8, 24), (10, 2, 12)])
+def test_gradients_match_central_differences_of_fp64_loss(env, orc, logn, bits, nseg):
+    """d loss / d parameter from the adjoint against central differences (h = 1e-3) of the
+    FP64 oracle loss at the same parameters: every gain component, taps and leakage terms
+    across the band, DC and Nyquist included, within 1e-3 relative."""
     torch, pol = env
-    n_fft, nseg, bits = 256, 24, 8
-    host, dev, n, w, g, d = _case(torch, n_fft, nseg, bits, 123)
+    n_fft = 1 << logn
+    host, dev, n, w, g, d = _case(torch, n_fft, nseg, bits, 123 + logn)
+    nb = n_fft // 2 + 1
+    st_ref, _ = orc.leak_forward(host, bits, n_fft, n, w, g, d)
+    target = (st_ref * 0.85).astype(np.float32)  # (the oracle's model, never the GPU's)
     with pol.Adjoint(n_fft, bits) as adj:
-        st = adj.run(dev, n, _t(torch, w), _t(torch, g), _t(torch, d))["stokes"]
-        target = (st * 0.85).contiguous()
-        r = adj.run(dev, n, _t(torch, w), _t(torch, g), _t(torch, d), target, grads=True)
-
-        def loss(w_, g_, d_):
-            out = adj.run(dev, n, _t(torch, w_), _t(torch, g_), _t(torch, d_), target)
-            return float(out["loss"].cpu()[0])
-
-        ggr = r["grad_gains"].cpu().numpy()
-        for i in range(4):
-            e = np.zeros(4, np.float32)
-            e[i] = 1e-3
-            fd = (loss(w, g + e, d) - loss(w, g - e, d)) / 2e-3
-            assert fd == pytest.approx(ggr[i], rel=1e-3, abs=1e-3 * np.abs(ggr).max())
-        gdr = r["grad_leak"].cpu().numpy()
-        for (f, k, c) in [(0, 3, 0), (0, 40, 1), (1, 7, 0), (1, 100, 1), (0, 0, 0), (1, 128, 0)]:
-            e = np.zeros_like(d)
-            e[f, k, c] = 1e-3
-            fd = (loss(w, g, d + e) - loss(w, g, d - e)) / 2e-3
-            assert fd == pytest.approx(gdr[f, k, c], rel=2e-3, abs=2e-3 * np.abs(gdr).max())
-        gwr = r["grad_window"].cpu().numpy()
-        for i in (0, 17, 128, 200, 255):
-            e = np.zeros_like(w)
-            e[i] = 1e-2
-            fd = (loss(w + e, g, d) - loss(w - e, g, d)) / 2e-2
-            assert fd == pytest.approx(gwr[i], rel=1e-2, abs=1e-2 * np.abs(gwr).max())
+        r = adj.run(dev, n, _t(torch, w), _t(torch, g), _t(torch, d), _t(torch, target), grads=True)
+        torch.cuda.synchronize()
+    _fd_checks(orc, host, bits, n_fft, n, w, g, d, target, r,
+               taps=(0, 1, n_fft // 3, n_fft // 2, n_fft - 1),
+               leaks=[(0, 0, 0), (0, 3, 0), (1, 7, 1), (0, nb // 2, 1), (1, nb - 1, 0)])
 
 
 def test_calibration_by_gradient_descent(env):

@@ -183,6 +183,43 @@ def test_unpack_bit_exact_every_code(pol, orc, bits):
     assert np.array_equal(got.astype(np.float64), ref)
 
 
+def _every_code_at_every_slot(n, bits):
+    """Codes with every value at every sample slot of a word: sample j of word w carries
+    (j + w (32/b + 1)) mod 2^b, and 32/b + 1 is odd, so w runs through all codes per slot."""
+    spw = 32 // bits
+    idx = np.arange(n, dtype=np.int64)
+    return ((idx % spw + (idx // spw) * (spw + 1)) % (1 << bits)).astype(np.uint8)
+
+
+@pytest.mark.parametrize("logn", [13, 14, 15, 16, 17, 18, 19, 20])
+@pytest.mark.parametrize("bits", [1, 2, 4, 8])
+def test_staged_decoder_bit_exact(pol, orc, logn, bits):
+    """From N = 2^13 up the FFT kernel decodes from a shared-memory stage with a rotation per
+    column and both IFs in one packed subtraction.  Through that device code (both stage
+    layouts, pairs with and without an IF b), every code at every rotation of the tile loop
+    decodes to exactly the oracle's level.  (1-bit at 2^19 and 2^20 is not staged: there the
+    kernel decodes per lane as spectrometer_debug_unpack, checked above.)"""
+    n_fft = 1 << logn
+    n = 2 * n_fft  # one segment of every code at every slot, one of random codes
+    rng = np.random.default_rng(50 + 10 * logn + bits)
+    ca = np.concatenate([_every_code_at_every_slot(n_fft, bits), synth.random_codes(rng, n_fft, bits)])
+    cb = np.concatenate([synth.random_codes(rng, n_fft, bits), _every_code_at_every_slot(n_fft, bits)[::-1]])
+    wa, wb = synth.pack(ca, bits), synth.pack(cb, bits)
+    ref_a, ref_b = orc.decode(bits, wa, n), orc.decode(bits, wb, n)
+    with pol.Spectrometer(2, bits, n_fft) as sp:
+        if bits == 1 and logn >= 19:
+            with pytest.raises(pol.PolarisError) as ei:
+                sp.debug_unpack_staged(wa, wb, n)
+            assert ei.value.code == pol.EINVAL
+            return
+        for layout in (0, 1):
+            ga, gb = sp.debug_unpack_staged(wa, wb, n, layout)
+            assert np.array_equal(ga.astype(np.float64), ref_a), (layout, "IF a")
+            assert np.array_equal(gb.astype(np.float64), ref_b), (layout, "IF b")
+            ga1, _ = sp.debug_unpack_staged(wa, None, n, layout)
+            assert np.array_equal(ga1.astype(np.float64), ref_a), (layout, "single IF")
+
+
 def test_integrate_without_segments_is_state_error(pol):
     with pol.Spectrometer(2, 2, 1024) as sp:
         with pytest.raises(pol.PolarisError) as ei:
