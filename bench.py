@@ -322,6 +322,24 @@ def run_reference(args, rank):
 # ------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------
+def assign_streams(work, n_lanes):
+    """Greedy longest-first schedule of independent jobs [(samples, n_fft)] onto n_lanes
+    streams: each job (heaviest first) goes to the lane with the least work so far.  A job's
+    work is its samples times a cost factor for transforms above 2^17 points, whose phase 1
+    costs more per point (measured: about 1.4x, 1.75x, 2.1x at 2^18, 2^19, 2^20)."""
+    def cost(n, n_fft):
+        return n * {1 << 18: 1.4, 1 << 19: 1.75, 1 << 20: 2.1}.get(n_fft, 1.0)
+
+    order = sorted(range(len(work)), key=lambda i: -cost(*work[i]))
+    load = [0.0] * n_lanes
+    lanes = [[] for _ in range(n_lanes)]
+    for i in order:
+        k = min(range(n_lanes), key=lambda j: load[j])
+        lanes[k].append(i)
+        load[k] += cost(*work[i])
+    return lanes
+
+
 def batch_graph_variant(torch, polaris, dev, local_rank, world, n_streams=64, seed=2024):
     """Many independent 2-IF spectrometers at once (a mixed multi-stream workload): N
     log-uniform in 2^12..2^20, 2- or 8-bit, 0.1..2 s of 16-Msps data each (whole segments),
@@ -347,10 +365,12 @@ def batch_graph_variant(torch, polaris, dev, local_rank, world, n_streams=64, se
         items.append((sp, dev_in, n, outs))
         total += 2 * n
 
-    # the handles spread over side streams (largest first, round robin) so that small
-    # transforms run side by side; forked from and joined back into the issuing stream
+    # the handles spread over side streams so that small transforms run side by side: longest
+    # first, each onto the side stream with the least work so far (work = samples, weighted by
+    # the per-sample cost of large transforms); forked from and joined back into the issuing
+    # stream
     side = [torch.cuda.Stream(dev) for _ in range(8)]
-    order = sorted(range(len(items)), key=lambda i: -items[i][2])
+    lanes = assign_streams([(items[i][2], items[i][0].n_fft) for i in range(len(items))], len(side))
 
     def issue_all(cs):
         fork = torch.cuda.Event()
@@ -358,7 +378,7 @@ def batch_graph_variant(torch, polaris, dev, local_rank, world, n_streams=64, se
         joins = []
         for k, ss in enumerate(side):
             ss.wait_event(fork)
-            for i in order[k::len(side)]:
+            for i in lanes[k]:
                 sp, dev_in, n, outs = items[i]
                 sp.feed(dev_in, n, on_device=True, stream=ss)
                 sp.integrate_device(*outs, stream=ss)
@@ -392,6 +412,13 @@ def batch_graph_variant(torch, polaris, dev, local_rank, world, n_streams=64, se
         ev1.record(stream)
     stream.synchronize()
     graph_ms = ev0.elapsed_time(ev1) / reps
+    # one more replay inside an NVTX range, for profilers (ncu --graph-profiling graph
+    # --nvtx --nvtx-include "batchreplay/")
+    torch.cuda.nvtx.range_push("batchreplay")
+    with torch.cuda.stream(stream):
+        g.replay()
+    stream.synchronize()
+    torch.cuda.nvtx.range_pop()
     launches = sum(sp.kernel_launches() for sp, *_ in items)
     for sp, *_ in items:
         sp.close()
@@ -853,6 +880,19 @@ def run_ours(args, rank, world, local_rank, dist):
     print(json.dumps(line), flush=True)
 
 
+def run_variant(name, local_rank):
+    """One variant alone (not the benchmark line): its JSON on one line."""
+    import torch
+
+    from paper_1412_1256_gb300 import polaris
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    polaris.load()
+    fn = {"batch_graph": batch_graph_variant, "tc_precision": tc_precision_variant, "adjoint": adjoint_variant}[name]
+    print(json.dumps({"variant": name, **fn(torch, polaris, dev, local_rank, 1)}), flush=True)
+
+
 def run_sweep(args, local_rank):
     """Throughput against N (--sweep LOGN,...): 4 IFs of --sweep-bits-bit samples, rectangular
     window, about 8 M samples per IF per step (whole segments), one handle on one stream,
@@ -923,11 +963,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-variants", action="store_true", help="skip the overlap / code-statistics variants")
     ap.add_argument("--sweep", default="", help="comma-separated log2 N: print the throughput against N instead")
+    ap.add_argument("--only", choices=["batch_graph", "tc_precision", "adjoint"], default=None,
+                    help="run one variant of the workload alone and print its JSON (for profiling)")
     ap.add_argument("--sweep-bits", type=int, default=2)
     ap.add_argument("--sweep-reps", type=int, default=20)
     args = ap.parse_args()
     if args.sweep:
         run_sweep(args, int(os.environ.get("LOCAL_RANK", "0")))
+        return
+    if args.only:
+        run_variant(args.only, int(os.environ.get("LOCAL_RANK", "0")))
         return
     if args.warmup < 3:
         args.warmup = 3

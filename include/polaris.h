@@ -166,6 +166,18 @@ int spectrometer_integrate_async(polaris_spec* s, const polaris_stokes_params* p
 int spectrometer_integrate_device(polaris_spec* s, const polaris_stokes_params* params, float* d_autos, float* d_cross,
                                   float* d_stokes, int64_t* n_segments_out, void* cuda_stream);
 
+/* Launch choices of a handle (not in the paper: how the transform is cut into kernel passes
+ * on this GPU).  spectrometer_get_launch reports the segments per kernel pass and the caps
+ * on CTAs per SM of the two FFT kernels (0: as many as fit); a handle created with
+ * max_batch_segments = 0 takes them from the library's tuned table (written by
+ * paper_1412_1256_gb300/tune.py from timings per N and width) or, for sizes without an
+ * entry, from the built-in rule.  spectrometer_set_launch_caps changes the two caps for
+ * later feeds (the tuner's knob; results do not depend on them).  Either output pointer may be
+ * NULL; POLARIS_EINVAL for a NULL handle or negative caps. */
+int spectrometer_get_launch(const polaris_spec* s, int* max_batch_segments, int* phase1_ctas_per_sm,
+                            int* phase2_ctas_per_sm);
+int spectrometer_set_launch_caps(polaris_spec* s, int phase1_ctas_per_sm, int phase2_ctas_per_sm);
+
 /* Number of output bins (N/2 + 1), IFs and pairs of a handle. */
 int64_t spectrometer_n_bins(const polaris_spec* s);
 int spectrometer_n_pairs(const polaris_spec* s);

@@ -15,6 +15,7 @@
 
 #include "../../include/polaris.h"
 #include "polaris_kernels.cuh"
+#include "polaris_tuning.h"
 
 namespace polaris {
 // per-size phase runners, one translation unit each (polaris_n<LOGN>.cu)
@@ -261,6 +262,7 @@ struct polaris_spec {
   int n_pair = 0, n_fpair = 0;
   int fa[kMaxIF], fb[kMaxIF], fcorr[kMaxIF];
   int max_batch = 0;
+  int cap1 = 0, cap2 = 0;  // CTAs per SM of phase 1 / phase 2 at most (0: as many as fit)
   int acc_copies = 1;
   float* d_taps = nullptr;
   float2* d_tw = nullptr;
@@ -536,12 +538,21 @@ extern "C" int spectrometer_create(const polaris_config* cfg, polaris_spec** out
   // batch size: segments per kernel pass.  Each pass pays a ramp and a tail on every SM, so
   // the default takes large passes (each slab half up to ~256 MB, at least 64 segments);
   // the slab then streams through HBM, which has bandwidth to spare for this path.
+  // (the tuned table, when it has an entry for this size and width, replaces the rule)
+  const TuneEntry* tuned = nullptr;
+  for (const TuneEntry& t : kTuned)
+    if (t.logn == logn && t.bits == c.bits) tuned = &t;
   if (c.max_batch_segments > 0) s->max_batch = c.max_batch_segments;
+  else if (tuned && tuned->max_batch > 0) s->max_batch = tuned->max_batch;
   else {
     const int64_t per_seg = (int64_t)nf * N * 8;
     int64_t mb = (256LL << 20) / per_seg;
     if (mb < 64) mb = 64;
     s->max_batch = (int)(mb > 4096 ? 4096 : mb);
+  }
+  if (c.max_batch_segments == 0 && tuned) {
+    s->cap1 = tuned->cap1;
+    s->cap2 = tuned->cap2;
   }
   s->slab_half = (size_t)s->max_batch * nf * N;
   s->carry_words_cap = N / spw;               // carried samples < N
@@ -554,7 +565,7 @@ extern "C" int spectrometer_create(const polaris_config* cfg, polaris_spec** out
   {
     const int P = plan_p(logn), Q2 = s->N2 / P, UPW = 16 / Q2;
     const int UGW = UPW > s->UPS ? 1 : s->UPS / UPW;
-    const long long warps = 2LL * s->num_sms * 8;  // phase-2 warps resident: two 8-warp CTAs per SM
+    const long long warps = (s->cap2 == 1 ? 1LL : 2LL) * s->num_sms * 8;  // phase-2 warps resident (8-warp CTAs)
     const long long nrg = warps / ((long long)nf * UGW);
     s->acc_copies = (int)(nrg / 64 < 1 ? 1 : (nrg / 64 > 16 ? 16 : nrg / 64));
   }
@@ -642,6 +653,7 @@ extern "C" const char* spectrometer_last_error(const polaris_spec* s) {
 }
 
 extern "C" int64_t spectrometer_n_bins(const polaris_spec* s) { return s ? s->nbin : -1; }
+
 extern "C" int spectrometer_n_pairs(const polaris_spec* s) { return s ? s->n_pair : -1; }
 
 static int check_usable(polaris_spec* s) {
@@ -772,6 +784,8 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
   a.tw = s->d_tw;
   a.acc = s->d_acc;
   a.acc_copies = s->acc_copies;
+  a.cap1 = s->cap1;
+  a.cap2 = s->cap2;
   a.fp64 = s->accum_fp64;
   a.bits = s->bits;
   a.num_sms = s->num_sms;
@@ -1031,6 +1045,26 @@ extern "C" int spectrometer_debug_unpack_staged(polaris_spec* s, const void* pac
 }
 
 extern "C" int64_t spectrometer_kernel_launches(const polaris_spec* s) { return s ? s->launches : -1; }
+
+extern "C" int spectrometer_set_launch_caps(polaris_spec* s, int phase1_ctas_per_sm, int phase2_ctas_per_sm) {
+  int rc = check_usable(s);
+  if (rc) return rc;
+  if (phase1_ctas_per_sm < 0 || phase2_ctas_per_sm < 0)
+    return set_err(s, POLARIS_EINVAL, "CTA caps must be >= 0 (0: as many as fit)");
+  s->cap1 = phase1_ctas_per_sm;
+  s->cap2 = phase2_ctas_per_sm;
+  return POLARIS_OK;
+}
+
+extern "C" int spectrometer_get_launch(const polaris_spec* s, int* max_batch_segments, int* phase1_ctas_per_sm,
+                                       int* phase2_ctas_per_sm) {
+  if (!s) return POLARIS_EINVAL;
+  if (max_batch_segments) *max_batch_segments = s->max_batch;
+  if (phase1_ctas_per_sm) *phase1_ctas_per_sm = s->cap1;
+  if (phase2_ctas_per_sm) *phase2_ctas_per_sm = s->cap2;
+  return POLARIS_OK;
+}
+
 
 extern "C" int spectrometer_set_profiling(polaris_spec* s, int on) {
   if (!s) return POLARIS_EINVAL;

@@ -80,6 +80,7 @@ struct BatchArgs {
   int fp64;
   int bits;
   int num_sms;
+  int cap1, cap2;       // CTAs per SM of phase 1 / phase 2 at most (0: as many as fit)
   int* err;             // device status word: set to 1 when a bounded wait ran out (see k_phase2)
   unsigned wait_limit;  // iterations of a bounded mbarrier wait before it counts as timed out
   // buffer extents, read only by the bounds-checked build (POLARIS_CHECK): float2 elements of
@@ -125,20 +126,34 @@ __device__ __forceinline__ void cp_async4(uint32_t dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// L2 eviction policies for the copy engine: the slab is written by phase 1 and read once by
+// phase 2 (kept in L2 in preference: evict_last); the packed input is read once (evict_first)
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(p));
+  return p;
+}
 // TMA store of a 2-D box (x = column, y = row) from shared memory, issued by one elected lane
 // of the (converged) warp as one bulk group; predicated, so the warp never branches apart
-__device__ __forceinline__ void tma_store_2d_elect(const CUtensorMap* map, const void* src, int x, int y) {
+__device__ __forceinline__ void tma_store_2d_elect(const CUtensorMap* map, const void* src, int x, int y,
+                                                   uint64_t policy) {
   asm volatile(
       "{\n .reg .pred p;\n .reg .b32 r;\n elect.sync r|p, 0xffffffff;\n"
-      " @p cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];\n"
+      " @p cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%2, %3}], [%1], %4;\n"
       " @p cp.async.bulk.commit_group;\n}\n" ::"l"(map),
-      "r"(smem_addr(src)), "r"(x), "r"(y)
+      "r"(smem_addr(src)), "r"(x), "r"(y), "l"(policy)
       : "memory");
 }
 // TMA store of a 2-D box by the calling thread alone (the caller commits the group)
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];\n" ::"l"(map), "r"(src),
-               "r"(x), "r"(y)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y, uint64_t policy) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%2, %3}], [%1], %4;\n" ::"l"(
+                   map),
+               "r"(src), "r"(x), "r"(y), "l"(policy)
                : "memory");
 }
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
@@ -306,8 +321,10 @@ __device__ __forceinline__ float2 p1_stage_decode(const uint32_t* sb, int row, i
 }
 
 __device__ __forceinline__ void corr_acc(float (&acc)[4], float2 U, float2 V) {
-  // S = 2X, D = 2iY;  |S|^2, |D|^2, Re/Im of i S conj(D) (= 4 X conj(Y))
-  const float sx = U.x + V.x, sy = U.y + V.y, dx = U.x - V.x, dy = U.y - V.y;
+  // S = 2X, D = 2iY;  |S|^2, |D|^2, Re/Im of i S conj(D) (= 4 X conj(Y)).  S and D by packed
+  // operations (each component rounds once, as the scalar sum and difference would)
+  const float2 S = __fadd2_rn(U, V), D = __ffma2_rn(V, make_float2(-1.f, -1.f), U);
+  const float sx = S.x, sy = S.y, dx = D.x, dy = D.y;
   acc[0] = fmaf(sx, sx, fmaf(sy, sy, acc[0]));
   acc[1] = fmaf(dx, dx, fmaf(dy, dy, acc[1]));
   acc[2] = fmaf(sx, dy, fmaf(-sy, dx, acc[2]));
@@ -409,6 +426,9 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
   }
   pdl_wait();  // the input and the slab may be touched from here on (dependent launch)
 
+  // Slab rows c > N1/2 are read by phase 2 only as the mirror column of unit N1 - c, which
+  // enters its transform conjugated: phase 1 stores them conjugated (an exact sign flip).
+  auto slab_val = [](float2 x, int c) { return c > N1 / 2 ? make_float2(x.x, -x.y) : x; };
   // the second half of the work on one column group: twiddle, transpose, Q1-point DFTs, store.
   // After the transpose lane (q1, cw) holds, for p = r Q1 + q1, the Q1 values of row p; its
   // DFT gives rows c = p + P m of the slab.
@@ -461,7 +481,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
             constexpr int m = decltype(m_)::value;
             uint32_t o = (uint32_t)(((r * Q1 + q1 + P * m) * JC + warp * CW + cw) * 8);
             o ^= ((o >> 7) & (uint32_t)ST::JSW) << 4;
-            *reinterpret_cast<float2*>(jb + o) = v[r * Q1 + m];
+            *reinterpret_cast<float2*>(jb + o) = slab_val(v[r * Q1 + m], r * Q1 + q1 + P * m);
           });
         });
         fence_async_shared();
@@ -469,7 +489,8 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
         if (tid == 0 && act) {  // xcol of warp 0 = the column group's first column
           sfor<0, N1 / BOXR>([&](auto h_) {
             constexpr int h = decltype(h_)::value;
-            tma_store_2d(&slab_map, smem_addr(jb + h * BOXR * JC * 8), xcol, (int)(g * N1 + h * BOXR));
+            tma_store_2d(&slab_map, smem_addr(jb + h * BOXR * JC * 8), xcol, (int)(g * N1 + h * BOXR),
+                         l2_evict_last());
           });
           bulk_commit();
         }
@@ -488,12 +509,12 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
           dit<Q1, r * Q1, 1>(v);
           sfor<0, Q1>([&](auto m_) {
             constexpr int m = decltype(m_)::value;
-            region[(r * Q1 + q1 + P * m) * CW + cw] = v[r * Q1 + m];
+            region[(r * Q1 + q1 + P * m) * CW + cw] = slab_val(v[r * Q1 + m], r * Q1 + q1 + P * m);
           });
         });
         fence_async_shared();
         __syncwarp();
-        if (act) tma_store_2d_elect(&slab_map, region, xcol, (int)(g * N1));
+        if (act) tma_store_2d_elect(&slab_map, region, xcol, (int)(g * N1), l2_evict_last());
       } else {
         sfor<0, PQ>([&](auto r_) {
           constexpr int r = decltype(r_)::value;
@@ -509,7 +530,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
             sfor<0, Q1>([&](auto m_) {
               constexpr int m = decltype(m_)::value;
               if (in_bounds(a.err, ((long long)g * N1 + p + (long long)m * P) * N2 + b, a.slab_elems))
-                dst[(size_t)m * P * N2] = u[m];
+                dst[(size_t)m * P * N2] = slab_val(u[m], p + m * P);
             });
           }
         });
@@ -520,7 +541,8 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
         float2* dst = a.scratch + (size_t)g * N1 * N2 + b;
         sfor<0, P>([&](auto p_) {
           constexpr int p = decltype(p_)::value;
-          if (in_bounds(a.err, (long long)g * N1 * N2 + (long long)p * N2 + b, a.slab_elems)) dst[(size_t)p * N2] = v[p];
+          if (in_bounds(a.err, (long long)g * N1 * N2 + (long long)p * N2 + b, a.slab_elems))
+            dst[(size_t)p * N2] = slab_val(v[p], p);
         });
       }
     }
@@ -600,18 +622,19 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
                    "r"(ib >= 0 ? 2 * box : box)
                    : "memory");
       const int x = (b0 * BITS) / 32;
+      const uint64_t pol_in = l2_evict_first();
       sfor<0, N1 / BOXR>([&](auto h_) {
         constexpr int h = decltype(h_)::value;
         asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-            "[%5];\n" ::"r"(dst + h * sub),
-            "l"(&in_maps.m[src][ia]), "r"(x), "r"(h * BOXR), "r"(z), "r"(bar)
+            "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, "
+            "{%2, %3, %4}], [%5], %6;\n" ::"r"(dst + h * sub),
+            "l"(&in_maps.m[src][ia]), "r"(x), "r"(h * BOXR), "r"(z), "r"(bar), "l"(pol_in)
             : "memory");
         if (ib >= 0)
           asm volatile(
-              "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-              "[%5];\n" ::"r"(dst + box + h * sub),
-              "l"(&in_maps.m[src][ib]), "r"(x), "r"(h * BOXR), "r"(z), "r"(bar)
+              "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, "
+              "{%2, %3, %4}], [%5], %6;\n" ::"r"(dst + box + h * sub),
+              "l"(&in_maps.m[src][ib]), "r"(x), "r"(h * BOXR), "r"(z), "r"(bar), "l"(pol_in)
               : "memory");
       });
     };
@@ -729,7 +752,8 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
 // ------------------------------------------------------------------------------------------
 // phase 2 and the correlator.  A warp owns UPW units (column u and its mirror N1 - u; unit 0
 // = columns 0 and N1/2) over a range of segments.  Lane (uw, e, q2) loads rows q2 + Q2 t of
-// its column, applies W_N^{b u} (its tensor-memory twiddles; the mirror conjugated), runs the
+// its column (a mirror column arrives conjugated: phase 1 stores rows c > N1/2 so), applies
+// W_N^{b u} (its tensor-memory twiddles), runs the
 // P-point DFT, transposes through the warp's region (the two members of a unit together),
 // applies W_N2^{q p} and runs the Q2-point DFTs, so that lane (uw, j) holds Z_k and
 // conj(Z_{N-k}) for bins k = u + N1 d, d = j PP + r + P m.  |S|^2, |D|^2 and i S conj(D)
@@ -758,14 +782,14 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
   }
   uint32_t parity = 0;
   bool stop = false;  // a bounded wait ran out: no further work, no flush
-  // the columns of units ug_ UPW .. ug_ UPW + UPW - 1 of segment s_ of FFT pair f_: unit w's
-  // column c and mirror N1 - c (0 and N1/2 for unit 0) at region columns 2w, 2w + 1
   // column c_ of segment s_ of pair f_; in the checked build an out-of-range column is recorded
   // and read from the slab's start instead (the barrier still receives its bytes)
   auto colp = [&](int f_, int s_, int c_) -> const float2* {
     const long long o = (((long long)s_ * a.n_fpair + f_) * N1 + c_) * N2;
     return a.scratch + (in_bounds(a.err, o + N2 - 1, a.slab_elems) ? o : 0);
   };
+  // the columns of units ug_ UPW .. ug_ UPW + UPW - 1 of segment s_ of FFT pair f_: unit w's
+  // column c and mirror N1 - c (0 and N1/2 for unit 0) at region columns 2w, 2w + 1
   auto prefetch = [&](int f_, int ug_, int s_) {
     if constexpr (UPW == 1) {
       const int u_ = ug_;
@@ -790,6 +814,19 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
 
   // lane roles: step 1 (uw, e, q2); step 2 (uw, j)
   const int uw = lane / (2 * Q2), e1 = (lane / Q2) & 1, q2 = lane % Q2, j = lane % (2 * Q2);
+  // Once a segment's columns have landed in shared memory their slab lines are dead (every
+  // column is read by exactly one warp, and the slab is rewritten before it is read again):
+  // drop them from L2 without a write-back, so that the slab's round trip costs no DRAM write
+  // for the lines still cached when they are read.  A column is N2 / 16 lines of 128 bytes;
+  // its Q2 lanes take P / 16 lines each.
+  static_assert(!PF || (P % 16 == 0 && (N2 * 8) % 128 == 0), "whole lines per lane");
+  auto discard = [&](int f_, int s_, int c_) {
+    const char* col = reinterpret_cast<const char*>(colp(f_, s_, c_));
+    sfor<0, P / 16>([&](auto i_) {
+      asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(col + (q2 + Q2 * decltype(i_)::value) * 128) : "memory");
+    });
+  };
+
   const int so = (SL > 1) ? uw / UPS : 0;
   const int uoff = (SL > 1) ? uw % UPS : uw;
 
@@ -813,7 +850,6 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
     const int u = (SL > 1) ? uoff : ug * UPW + uoff;
     const int c = (u == 0) ? (e1 ? N1 / 2 : 0) : (e1 ? N1 - u : u);
     const int tu = (u == 0 && e1) ? N1 / 2 : u;
-    const float sgn = (e1 && u != 0) ? -1.0f : 1.0f;
     const bool special = (u == 0);
     const bool warp_special = (SL > 1) || (ug == 0);  // some lane of this warp holds unit 0
     // tensor memory: zero the accumulators, load this lane's twiddles W_N^{b tu}, b = q2 + Q2 t
@@ -896,10 +932,8 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
         sfor<0, 8>([&](auto k_) {
           constexpr int k = decltype(k_)::value;
           constexpr int t = 8 * cc + k;
-          if constexpr (t < P) {
-            float2 z = v[ct::bitrev(t, P)];
-            z.y *= sgn;  // mirror column: conjugate
-            v[ct::bitrev(t, P)] = cmul(z, make_float2(w16[2 * k], w16[2 * k + 1]));
+          if constexpr (t < P) {  // (a mirror column arrives conjugated from phase 1)
+            v[ct::bitrev(t, P)] = cmul(v[ct::bitrev(t, P)], make_float2(w16[2 * k], w16[2 * k + 1]));
           }
         });
       });
@@ -994,6 +1028,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
         __syncwarp();  // mirror area read before the next transpose
         next_prefetch(rnd);
       }
+      if constexpr (PF) discard(f, s, c);  // (this segment's copy completed at the wait above)
     }
     if (stop) break;
     // flush this lane's sums into the integration accumulators (native order; the range's copy)
@@ -1217,7 +1252,8 @@ static cudaError_t launch_phase1(const BatchArgs& a, cudaStream_t st, bool pdl) 
   // staged: one unit (a tile, or half of one in the last round) per CTA pass
   const long long ctas = ST::STAGED ? (cols / ST::TILE) * ST::IPT
                                      : ((cols + PL::CW - 1) / PL::CW + PL::WARPS - 1) / PL::WARPS;
-  const long long cap = (long long)per_sm * a.num_sms;
+  const int eff = (a.cap1 > 0 && a.cap1 < per_sm) ? a.cap1 : per_sm;
+  const long long cap = (long long)eff * a.num_sms;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(ctas < cap ? ctas : cap));
   cfg.blockDim = dim3(PL::THREADS);
@@ -1258,7 +1294,8 @@ cudaError_t run_phase2(const BatchArgs& a, cudaStream_t st, bool pdl) {
     per_sm = ctas_per_sm(k_phase2<LOGN>, PL::THREADS, PL::SMEM2, PL::TCOLS2);
     attr_dev = dev;
   }
-  const long long warps = (long long)per_sm * a.num_sms * PL::WARPS;
+  const int eff = (a.cap2 > 0 && a.cap2 < per_sm) ? a.cap2 : per_sm;
+  const long long warps = (long long)eff * a.num_sms * PL::WARPS;
   const int R = (a.nseg + PL::SL - 1) / PL::SL;
   const long long groups = (long long)a.n_fpair * PL::UGW;
   // as many segment ranges per (pair, unit group) as leave every warp at most one item; the
@@ -1270,7 +1307,7 @@ cudaError_t run_phase2(const BatchArgs& a, cudaStream_t st, bool pdl) {
   const long long range_len = (R + nrg - 1) / nrg;  // rounds per item
   const long long n_items = groups * ((R + range_len - 1) / range_len);
   const long long ctas = (n_items + PL::WARPS - 1) / PL::WARPS;
-  const long long cap = (long long)per_sm * a.num_sms;
+  const long long cap = (long long)eff * a.num_sms;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(ctas < cap ? ctas : cap));
   cfg.blockDim = dim3(PL::THREADS);

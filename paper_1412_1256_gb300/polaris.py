@@ -33,6 +33,7 @@ EXPORTS = (
     "spectrometer_set_profiling", "spectrometer_kernel_times", "spectrometer_run_noalloc",
     "spectrometer_code_histogram", "polaris_power_from_histogram", "polaris_set_wait_limit",
     "spectrometer_integrate_async", "polaris_checked_build", "polaris_set_check_understate",
+    "spectrometer_get_launch", "spectrometer_set_launch_caps",
     "polaris_adj_create", "polaris_adj_run", "polaris_adj_destroy", "polaris_adj_last_error",
     "polaris_tc_create", "polaris_tc_feed", "polaris_tc_integrate", "polaris_tc_set_wait_limit",
     "polaris_tc_destroy", "polaris_tc_last_error",
@@ -86,6 +87,10 @@ def load(path: str = LIB_PATH):
             lib.spectrometer_integrate_async.restype = ci
             lib.spectrometer_n_bins.argtypes = [vp]
             lib.spectrometer_n_bins.restype = i64
+            lib.spectrometer_get_launch.argtypes = [vp] + [ctypes.POINTER(ci)] * 3
+            lib.spectrometer_get_launch.restype = ci
+            lib.spectrometer_set_launch_caps.argtypes = [vp, ci, ci]
+            lib.spectrometer_set_launch_caps.restype = ci
             lib.spectrometer_n_pairs.argtypes = [vp]
             lib.spectrometer_n_pairs.restype = ci
             lib.spectrometer_debug_unpack.argtypes = [vp, vp, i64, vp]
@@ -317,6 +322,16 @@ class Spectrometer:
                                                         ctypes.byref(nseg), _stream_ptr(stream)))
         del g
         return int(nseg.value)
+
+    def launch_choices(self) -> dict:
+        """Segments per kernel pass and the CTA-per-SM caps of the two FFT kernels (0: as many
+        as fit), as the handle uses them."""
+        mb, c1, c2 = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(load().spectrometer_get_launch(self._h, ctypes.byref(mb), ctypes.byref(c1), ctypes.byref(c2)))
+        return {"max_batch_segments": mb.value, "phase1_ctas_per_sm": c1.value, "phase2_ctas_per_sm": c2.value}
+
+    def set_launch_caps(self, phase1_ctas_per_sm: int, phase2_ctas_per_sm: int) -> None:
+        self._check(load().spectrometer_set_launch_caps(self._h, int(phase1_ctas_per_sm), int(phase2_ctas_per_sm)))
 
     def kernel_launches(self) -> int:
         return int(load().spectrometer_kernel_launches(self._h))
