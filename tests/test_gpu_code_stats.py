@@ -79,7 +79,11 @@ def test_power_estimates_match_oracle(pol, orc, bits):
     packed = [synth.pack(codes, bits)]
     with pol.Spectrometer(1, bits, 1 << 12, code_stats=True) as sp:
         sp.feed(packed, 1 << 18)
-        h = sp.code_histogram()[0]
+        h_gpu = sp.code_histogram()[0]
+    # both estimators take the oracle's histogram (an oracle input never comes from the GPU);
+    # the GPU's histogram must equal it
+    h = orc.code_histogram(packed, bits, 1 << 12, 1 << 18)[0]
+    assert np.array_equal(np.asarray(h_gpu, np.uint64), np.asarray(h, np.uint64))
     m2, sg = pol.power_from_histogram(bits, h)
     m2_ref, sg_ref = orc.power(bits, h)
     assert m2 == pytest.approx(m2_ref, rel=1e-13)
