@@ -684,7 +684,7 @@ def run_ours(args, rank, world, local_rank, dist):
     # spectrometer handles on L streams take steps in turn, so that copies and kernels of
     # consecutive integrations overlap (a streaming caller's pattern); the host waits for
     # step i's outputs after queueing step i + L - 1.
-    e2e_value = None
+    e2e_value, e2e_spread = None, None
     if not args.no_e2e:
         n_host = min(len(unique), 4)
         pinned = [torch.from_numpy(unique[i]).pin_memory() for i in range(n_host)]
@@ -716,18 +716,33 @@ def run_ours(args, rank, world, local_rank, dist):
             assert e2e_issue(i) == SEGS
             e2e_wait(i)
         e2e_steps = max(3, min(args.steps, args.e2e_steps))
-        torch.cuda.synchronize(dev)
-        barrier()
-        t0 = time.perf_counter()
-        for i in range(min(L - 1, e2e_steps)):
-            assert e2e_issue(i) == SEGS
-        for i in range(e2e_steps):
-            if i + L - 1 < e2e_steps:
-                assert e2e_issue(i + L - 1) == SEGS
-            e2e_wait(i)  # step i's spectra are in host memory
-        torch.cuda.synchronize(dev)
-        dt = slowest(dist, time.perf_counter() - t0)
+
+        def e2e_block(base):
+            """One end-to-end timed region of e2e_steps steps (host clock, synchronised on both
+            sides); returns the slowest rank's seconds."""
+            torch.cuda.synchronize(dev)
+            barrier()
+            t0 = time.perf_counter()
+            for i in range(min(L - 1, e2e_steps)):
+                assert e2e_issue(base + i) == SEGS
+            for i in range(e2e_steps):
+                if i + L - 1 < e2e_steps:
+                    assert e2e_issue(base + i + L - 1) == SEGS
+                e2e_wait(base + i)  # step i's spectra are in host memory
+            torch.cuda.synchronize(dev)
+            return slowest(dist, time.perf_counter() - t0)
+
+        # repeated like the device-resident region; the median region gives the value
+        e2e_blocks = [e2e_block(0)]
+        e2e_reps = max(args.repeats, int(math.ceil(args.min_timed_ms * 1e-3 / max(e2e_blocks[0], 1e-6))))
+        e2e_reps = min(e2e_reps, max(args.repeats, 2000))
+        while len(e2e_blocks) < e2e_reps:
+            e2e_blocks.append(e2e_block(len(e2e_blocks) * e2e_steps))
+        dt = float(statistics.median(e2e_blocks))
         e2e_value = whole_job_rate(world, e2e_steps, SAMPLES_PER_STEP, dt)
+        e2e_spread = {"repeats": len(e2e_blocks), "steps_per_region": e2e_steps,
+                      "min_ms_per_step": min(e2e_blocks) * 1e3 / e2e_steps,
+                      "max_ms_per_step": max(e2e_blocks) * 1e3 / e2e_steps}
         for ln in lanes[1:]:
             ln[0].close()
 
@@ -850,7 +865,7 @@ def run_ours(args, rank, world, local_rank, dist):
         },
         "kernels": kernels,
         "e2e": {"value": e2e_value, "unit": "Msample/s", "h2d_bytes_per_step": H2D_BYTES,
-                "d2h_bytes_per_step": D2H_BYTES},
+                "d2h_bytes_per_step": D2H_BYTES, "spread": e2e_spread},
         "gpu_launches": int(round(launches)),
         "gpu_launches_note": "kernels of ours launched per timed region of `steps` steps (the mean over the repeats)",
         "repeats": spread["repeats"],
