@@ -61,6 +61,10 @@ CONFIG = {
     "l2": "inputs larger than L2: 60 distinct seconds (480 MB ring) cycled, each step reads another second",
 }
 DEFAULT_HANDLES, DEFAULT_E2E_HANDLES = 3, 6
+# With several integrations in flight, at most one phase-1 CTA per SM leaves every SM room for
+# another integration's phase 2 (shared-memory-bound work beside FP32-bound work): 594k against
+# 578k-583k Msample/s with three handles (one handle alone is 6% slower with the cap).
+DEFAULT_CAPS = "1,0"
 
 
 # ------------------------------------------------------------------------------------------
@@ -340,7 +344,7 @@ def assign_streams(work, n_lanes):
     return lanes
 
 
-def batch_graph_variant(torch, polaris, dev, local_rank, world, n_streams=64, seed=2024):
+def batch_graph_variant(torch, polaris, dev, local_rank, world, n_streams=64, seed=2024, caps=None):
     """Many independent 2-IF spectrometers at once (a mixed multi-stream workload): N
     log-uniform in 2^12..2^20, 2- or 8-bit, 0.1..2 s of 16-Msps data each (whole segments),
     every handle's feed + integrate captured into one CUDA graph and replayed; reports the
@@ -362,6 +366,8 @@ def batch_graph_variant(torch, polaris, dev, local_rank, world, n_streams=64, se
         outs = (torch.empty((2, nb), device=dev), torch.empty((1, nb, 2), device=dev),
                 torch.empty((1, 4, nb), device=dev))
         sp = polaris.Spectrometer(2, bits, n_fft, device=local_rank, max_batch_segments=nseg)
+        if caps:
+            sp.set_launch_caps(*caps)
         items.append((sp, dev_in, n, outs))
         total += 2 * n
 
@@ -423,6 +429,7 @@ def batch_graph_variant(torch, polaris, dev, local_rank, world, n_streams=64, se
     for sp, *_ in items:
         sp.close()
     return {"streams": n_streams, "samples_per_pass": total, "graph_ms_per_pass": graph_ms,
+            "ctas_per_sm_caps": list(caps) if caps else "library default",
             "eager_ms_per_pass": eager_ms, "value": world * total / (graph_ms * 1e-3) / 1e6,
             "eager_value": world * total / (eager_ms * 1e-3) / 1e6, "unit": "Msample/s",
             "note": "N log-uniform 2^12..2^20, 2/8-bit, 0.1..2 s at 16 Msps (whole segments), seed 2024"}
@@ -616,6 +623,10 @@ def run_ours(args, rank, world, local_rank, dist):
         if dist is not None:
             dist.barrier()
 
+    if args.caps:
+        c1, c2 = (int(x) for x in args.caps.split(","))
+        for hd in handles:
+            hd[0].set_launch_caps(c1, c2)
     for i in range(max(args.warmup, H)):
         assert step(i) == SEGS
     torch.cuda.synchronize(dev)
@@ -668,7 +679,11 @@ def run_ours(args, rank, world, local_rank, dist):
               "note": f"{len(blocks)} timed regions of {args.steps} steps each; value and ms_per_step are "
                       f"the median region's"}
 
-    # per-kernel device time: a second timed pass with every launch bracketed by events
+    # per-kernel device time: a second timed pass with every launch bracketed by events, one
+    # handle on one stream, each kernel alone at its default occupancy (the CTA caps are a
+    # policy for integrations in flight side by side)
+    if args.caps:
+        sp.set_launch_caps(0, 0)
     sp.set_profiling(True)
     prof_steps = max(3, min(args.steps, 50))
     for i in range(prof_steps):
@@ -676,6 +691,8 @@ def run_ours(args, rank, world, local_rank, dist):
     torch.cuda.synchronize(dev)
     kt = sp.kernel_times()
     sp.set_profiling(False)
+    if args.caps:
+        sp.set_launch_caps(*(int(x) for x in args.caps.split(",")))
 
     # e2e through the C ABI with pinned host buffers: every step copies its input from
     # pinned host memory (feed with host pointers, asynchronous mode: the copy is queued and
@@ -694,6 +711,8 @@ def run_ours(args, rank, world, local_rank, dist):
         for k in range(L):
             spk = sp if k == 0 else polaris.Spectrometer(N_IF, BITS, N_FFT, device=local_rank,
                                                          max_batch_segments=args.batch_segments)
+            if args.caps:
+                spk.set_launch_caps(*(int(x) for x in args.caps.split(",")))
             stk = torch.cuda.Stream(dev)
             dev_out = (torch.empty((N_IF, NBIN), dtype=torch.float32, device=dev),
                        torch.empty((N_PAIR, NBIN, 2), dtype=torch.float32, device=dev),
@@ -758,6 +777,9 @@ def run_ours(args, rank, world, local_rank, dist):
             hs = [(make(), stream if k == 0 else torch.cuda.Stream(dev),
                    (autos, cross, stokes) if k == 0 else
                    (torch.empty_like(autos), torch.empty_like(cross), torch.empty_like(stokes))) for k in range(H)]
+            if args.caps:
+                for hd in hs:
+                    hd[0].set_launch_caps(*(int(x) for x in args.caps.split(",")))
 
             def stepv(i):
                 spv, st, outs = hs[i % H]
@@ -808,7 +830,8 @@ def run_ours(args, rank, world, local_rank, dist):
         variants["code_stats"] = {"ms_per_step": ms, "value": world * SAMPLES_PER_STEP / (ms * 1e-3) / 1e6,
                                   "unit": "Msample/s", "steps": nv, "handles": H,
                                   "histogram_kernel_ms": kh[0] / kh[1] if kh[1] else None}
-        variants["batch_graph"] = batch_graph_variant(torch, polaris, dev, local_rank, world)
+        caps = tuple(int(x) for x in args.caps.split(",")) if args.caps else None
+        variants["batch_graph"] = batch_graph_variant(torch, polaris, dev, local_rank, world, caps=caps)
         variants["adjoint"] = adjoint_variant(torch, polaris, dev, local_rank, world)
         variants["tc_precision"] = tc_precision_variant(torch, polaris, dev, local_rank, world)
 
@@ -872,9 +895,11 @@ def run_ours(args, rank, world, local_rank, dist):
         "spread": spread,
         "clocks": clocks,
         "pipeline": {"handles": H, "e2e_handles": None if args.no_e2e else max(2, args.e2e_handles),
+                     "ctas_per_sm_caps": args.caps or "library default",
                      "note": "consecutive steps (independent 1-s integrations) alternate over this many "
-                             "spectrometer handles, each on its own stream; per-kernel times come from a "
-                             "separate pass of one handle on one stream"},
+                             "spectrometer handles, each on its own stream, with the CTA-per-SM caps above; "
+                             "per-kernel times come from a separate pass of one handle on one stream, each "
+                             "kernel alone at its default occupancy"},
     }
     if variants is not None:
         for v in ("forward_loss", "forward_adjoint"):
@@ -895,7 +920,7 @@ def run_ours(args, rank, world, local_rank, dist):
     print(json.dumps(line), flush=True)
 
 
-def run_variant(name, local_rank):
+def run_variant(name, local_rank, caps=""):
     """One variant alone (not the benchmark line): its JSON on one line."""
     import torch
 
@@ -905,7 +930,8 @@ def run_variant(name, local_rank):
     torch.cuda.set_device(dev)
     polaris.load()
     fn = {"batch_graph": batch_graph_variant, "tc_precision": tc_precision_variant, "adjoint": adjoint_variant}[name]
-    print(json.dumps({"variant": name, **fn(torch, polaris, dev, local_rank, 1)}), flush=True)
+    kw = {"caps": tuple(int(x) for x in caps.split(","))} if (name == "batch_graph" and caps) else {}
+    print(json.dumps({"variant": name, **fn(torch, polaris, dev, local_rank, 1, **kw)}), flush=True)
 
 
 def run_sweep(args, local_rank):
@@ -972,6 +998,9 @@ def main():
                     help="reference arm: about this many seconds of oracle work over warmup + steps")
     ap.add_argument("--cpu-repeats", type=int, default=8,
                     help="CPU baseline: passes over --cpu-segs segments, split over the host cores")
+    ap.add_argument("--caps", default=DEFAULT_CAPS,
+                    help="P1,P2: CTAs per SM of the two FFT kernels at most, for every handle of the timed and "
+                         "end-to-end loops (0: as many as fit; empty: the library's choice)")
     ap.add_argument("--batch-segments", type=int, default=0,
                     help="segments per kernel pass (0: the library's default, sized to keep the slab in L2)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -987,7 +1016,7 @@ def main():
         run_sweep(args, int(os.environ.get("LOCAL_RANK", "0")))
         return
     if args.only:
-        run_variant(args.only, int(os.environ.get("LOCAL_RANK", "0")))
+        run_variant(args.only, int(os.environ.get("LOCAL_RANK", "0")), args.caps)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -172,8 +172,11 @@ int spectrometer_integrate_device(polaris_spec* s, const polaris_stokes_params* 
  * max_batch_segments = 0 takes them from the library's tuned table (written by
  * paper_1412_1256_gb300/tune.py from timings per N and width) or, for sizes without an
  * entry, from the built-in rule.  spectrometer_set_launch_caps changes the two caps for
- * later feeds (the tuner's knob; results do not depend on them).  Either output pointer may be
- * NULL; POLARIS_EINVAL for a NULL handle or negative caps. */
+ * later feeds (results do not depend on them).  A caller that keeps several integrations in
+ * flight on separate handles and streams gains by capping phase 1 at one CTA per SM: every SM
+ * then keeps room for another integration's phase 2 (about 3% at N = 2^17 with three
+ * handles, while one handle alone is about 6% slower with that cap).  Either output pointer
+ * may be NULL; POLARIS_EINVAL for a NULL handle or negative caps. */
 int spectrometer_get_launch(const polaris_spec* s, int* max_batch_segments, int* phase1_ctas_per_sm,
                             int* phase2_ctas_per_sm);
 int spectrometer_set_launch_caps(polaris_spec* s, int phase1_ctas_per_sm, int phase2_ctas_per_sm);
