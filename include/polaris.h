@@ -121,7 +121,12 @@ typedef struct {
 int spectrometer_create(const polaris_config* cfg, polaris_spec** out);
 
 /* Feed n_samples_per_if new samples of every IF stream and accumulate all whole
- * segments they complete into the current integration.
+ * segments they complete into the current integration.  This is the GPU side of the
+ * paper's data path (Sec. 2, Fig. 2 caption): the sampler's quantised IF streams
+ * (Table 1: four IFs, 4- or 8-bit samples at 8 or 16 Msps) are translated to floats, cut
+ * into segments, transformed, multiplied into power and cross-power spectra, and added to
+ * the running integration (function (4) of Sec. 2: integration over the 1-s time
+ * resolution of Table 1, closed by spectrometer_integrate).
  *   packed[i]   pointer to IF i's words (n_samples_per_if * bits / 32 words), 4-byte
  *               aligned, in the memory that on_device names:
  *   on_device   POLARIS_INPUT_HOST (0): host memory, read when the call returns;

@@ -724,7 +724,7 @@ extern "C" int spectrometer_feed(polaris_spec* s, const void* const* packed, int
       s->in_words_cap = nw;
     }
     // IF streams at one constant stride (rows of one host array, say) go over in one
-    // pitched copy: one API call instead of one per IF (each costs host time).  The driver
+    // pitched copy: one API call instead of one per IF (each costs host time).  The CUDA driver
     // refuses (at the call, queueing nothing) a pitched copy whose rows lie in different
     // pinned allocations; then the streams go one by one.
     const long long stride = s->n_if > 1 ? (long long)((const char*)packed[1] - (const char*)packed[0]) : 0;
