@@ -344,7 +344,7 @@ def assign_streams(work, n_lanes):
     return lanes
 
 
-def batch_graph_variant(torch, polaris, dev, local_rank, world, n_streams=64, seed=2024, caps=None):
+def batch_graph_variant(torch, polaris, dev, local_rank, world, n_streams=64, seed=2024, caps=None, n_side=8):
     """Many independent 2-IF spectrometers at once (a mixed multi-stream workload): N
     log-uniform in 2^12..2^20, 2- or 8-bit, 0.1..2 s of 16-Msps data each (whole segments),
     every handle's feed + integrate captured into one CUDA graph and replayed; reports the
@@ -375,7 +375,7 @@ def batch_graph_variant(torch, polaris, dev, local_rank, world, n_streams=64, se
     # first, each onto the side stream with the least work so far (work = samples, weighted by
     # the per-sample cost of large transforms); forked from and joined back into the issuing
     # stream
-    side = [torch.cuda.Stream(dev) for _ in range(8)]
+    side = [torch.cuda.Stream(dev) for _ in range(n_side)]
     lanes = assign_streams([(items[i][2], items[i][0].n_fft) for i in range(len(items))], len(side))
 
     def issue_all(cs):
