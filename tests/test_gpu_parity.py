@@ -249,3 +249,42 @@ def test_alloc_limit_gives_enomem(pol):
         pol.set_alloc_limit(-1)
     with pol.Spectrometer(4, 2, 1024):
         pass
+
+
+def test_precision_workload_full_size_fp32_path(pol, orc):
+    """The precision workload at full size through the FP32 path, as the benchmark times it:
+    2 IFs, int8, 262144-point segments, Hann window, 610 segments (10 s at 16 Msps) in one
+    feed of device-resident input on one handle.  Like the benchmark's ring, segment s is a
+    copy of distinct segment s mod 16, so the expected sums are the oracle's sums over the 16
+    distinct segments, each weighted by its number of copies (sums of identical terms, and
+    Stokes linear in the sums, with unit gains and psi = 0)."""
+    torch = pytest.importorskip("torch")
+    packed, cfg = synth.config_precision(seed=1256, n_segments=16)
+    n_fft, n_u, nseg = cfg["n_fft"], 16, 610
+    wps = n_fft // 4  # int8: four samples per word
+    ring = []
+    for p in packed:
+        big = np.empty(nseg * wps, np.uint32)
+        for s in range(nseg):
+            u = s % n_u
+            big[s * wps:(s + 1) * wps] = p[u * wps:(u + 1) * wps]
+        ring.append(torch.from_numpy(big.view(np.int32)).cuda())
+    nb = n_fft // 2 + 1
+    autos = torch.zeros((2, nb), device="cuda")
+    cross = torch.zeros((1, nb, 2), device="cuda")
+    stokes = torch.zeros((1, 4, nb), device="cuda")
+    st = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with pol.Spectrometer(2, 8, n_fft, window="hann") as sp:
+        sp.feed(ring, nseg * n_fft, on_device=True, stream=st)
+        assert sp.integrate_device(autos, cross, stokes, stream=st) == nseg
+        st.synchronize()
+    ref = {"autos": 0.0, "cross": 0.0, "stokes": 0.0}
+    for u in range(n_u):
+        w = len(range(u, nseg, n_u))
+        r = orc.spectrometer([p[u * wps:(u + 1) * wps] for p in packed], 8, n_fft, n_fft, window_kind=1)
+        for key in ref:
+            ref[key] = ref[key] + w * np.asarray(r[key])
+    c = cross.cpu().numpy()
+    got = {"autos": autos.cpu().numpy(), "cross": c[..., 0] + 1j * c[..., 1], "stokes": stokes.cpu().numpy()}
+    assert_close(got, ref, [(0, 1)], TOL)
