@@ -192,6 +192,152 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
+class _GpmInfo(ctypes.Structure):
+    _fields_ = [("shortName", ctypes.c_char_p), ("longName", ctypes.c_char_p), ("unit", ctypes.c_char_p)]
+
+
+class _GpmMetric(ctypes.Structure):
+    _fields_ = [("metricId", ctypes.c_uint), ("nvmlReturn", ctypes.c_int), ("value", ctypes.c_double),
+                ("metricInfo", _GpmInfo)]
+
+
+class _GpmMetricsGet(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_uint), ("numMetrics", ctypes.c_uint), ("sample1", ctypes.c_void_p),
+                ("sample2", ctypes.c_void_p), ("metrics", _GpmMetric * 210)]
+
+
+class LiveCounters:
+    """Read-only NVML GPU performance-monitoring (GPM) counters over a stretch of live work:
+    two counter samples around a region that runs unprofiled and unserialised, so the
+    figures describe the schedule the timed region runs (kernels of several streams side by
+    side), which a kernel profiler replaying launches one at a time does not see.  NVML
+    reports DRAM bandwidth as a percentage of a theoretical maximum; bytes come from
+    calibrating that percentage with a device copy of known size measured the same way."""
+    METRICS = {"dram_bw_util_pct": 10, "sm_util_pct": 2, "sm_occupancy_pct": 3, "fp32_util_pct": 12}
+
+    def __init__(self, cuda_index: int):
+        self.ok, self.why = False, ""
+        try:
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            if lib.nvmlInit_v2() != 0:
+                self.why = "nvmlInit failed"
+                return
+            index = cuda_index
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            if vis:
+                ids = [v.strip() for v in vis.split(",") if v.strip()]
+                if cuda_index < len(ids) and ids[cuda_index].isdigit():
+                    index = int(ids[cuda_index])
+            h = ctypes.c_void_p()
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(h)) != 0:
+                self.why = "no NVML handle"
+                return
+            sup = (ctypes.c_uint * 2)(1, 0)  # {version, isSupportedDevice}
+            if lib.nvmlGpmQueryDeviceSupport(h, sup) != 0 or not sup[1]:
+                self.why = "GPM not supported on this device"
+                return
+            self.samples = [ctypes.c_void_p(), ctypes.c_void_p()]
+            for smp in self.samples:
+                if lib.nvmlGpmSampleAlloc(ctypes.byref(smp)) != 0:
+                    self.why = "nvmlGpmSampleAlloc failed"
+                    return
+            self.lib, self.h, self.ok = lib, h, True
+        except (OSError, AttributeError) as e:
+            self.why = f"NVML GPM unavailable: {e}"
+
+    def measure(self, torch, dev, run, prefill: int, min_s: float = 1.0):
+        """Counters over a stretch of steady work: `prefill` calls of `run()` are queued before
+        the first sample and more are queued until min_s seconds have passed on the host, so
+        the device is busy with the same work at both samples (the counters' own sampling
+        instants then do not matter); NVML wants more than 100 ms between samples."""
+        torch.cuda.synchronize(dev)
+        for _ in range(prefill):
+            run()
+        if self.lib.nvmlGpmSampleGet(self.h, self.samples[0]) != 0:
+            return None
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < min_s:
+            run()
+        if self.lib.nvmlGpmSampleGet(self.h, self.samples[1]) != 0:
+            return None
+        torch.cuda.synchronize(dev)
+        mg = _GpmMetricsGet()
+        mg.version, mg.numMetrics = 1, len(self.METRICS)
+        mg.sample1, mg.sample2 = self.samples[0].value, self.samples[1].value
+        for k, mid in enumerate(self.METRICS.values()):
+            mg.metrics[k].metricId = mid
+        if self.lib.nvmlGpmMetricsGet(ctypes.byref(mg)) != 0:
+            return None
+        return {name: (float(mg.metrics[k].value) if mg.metrics[k].nvmlReturn == 0 else None)
+                for k, name in enumerate(self.METRICS)}
+
+    def close(self):
+        if self.ok:
+            for smp in self.samples:
+                self.lib.nvmlGpmSampleFree(smp)
+
+
+def _event_ms(torch, dev, run, calls: int) -> float:
+    """Device milliseconds per call of `run()` (events on the current stream, after warm-up)."""
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        run()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    a.record(stream)
+    for _ in range(calls):
+        run()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    return a.elapsed_time(b) / calls
+
+
+def live_dram(torch, dev, cuda_index, run, ms_per_call, units_per_call, unit_name):
+    """DRAM bytes per unit of live work from NVML's DRAM-bandwidth percentage, taken in a
+    steady state.  The percentage is turned into bytes per second with streams of known
+    traffic on 1 GiB buffers (a copy: 2 GiB per call; a fill: 1 GiB written; a sum: 1 GiB
+    read), each timed with events and sampled the same way; their agreement shows how
+    linear the percentage is in bytes.  ms_per_call is the work's own measured time."""
+    lc = LiveCounters(cuda_index)
+    if not lc.ok:
+        return {"unavailable": lc.why}
+    try:
+        gib = 1 << 30
+        src = torch.empty(gib // 4, dtype=torch.float32, device=dev).fill_(1.0)
+        dst = torch.empty_like(src)
+        acc = torch.empty((), dtype=torch.float32, device=dev)
+        streams = {"copy": (lambda: dst.copy_(src), 2 * gib), "write": (lambda: dst.fill_(2.0), gib),
+                   "read": (lambda: torch.sum(src, 0, out=acc), gib)}
+        cal = {}
+        for name, (fn, nbytes) in streams.items():
+            ms = _event_ms(torch, dev, fn, 20)
+            m = lc.measure(torch, dev, fn, prefill=int(60 / ms) + 1)
+            if not m or not m["dram_bw_util_pct"]:
+                return {"unavailable": f"GPM metrics not returned ({name})"}
+            gbs = nbytes / (ms * 1e-3) / 1e9
+            cal[name] = {"gbs": gbs, "dram_bw_util_pct": m["dram_bw_util_pct"],
+                         "gbs_per_pct": gbs / m["dram_bw_util_pct"]}
+        del src, dst
+        work = lc.measure(torch, dev, run, prefill=int(60 / ms_per_call) + 1)
+        if not work or work["dram_bw_util_pct"] is None:
+            return {"unavailable": "GPM metrics not returned (work)"}
+        gbs_per_pct = cal["copy"]["gbs_per_pct"]
+        gbs = gbs_per_pct * work["dram_bw_util_pct"]
+        per_unit = gbs * 1e9 * (ms_per_call * 1e-3) / units_per_call
+        spread = [c["gbs_per_pct"] for c in cal.values()]
+        return {f"dram_bytes_per_{unit_name}": per_unit, "dram_gbs": gbs,
+                f"dram_bytes_per_{unit_name}_range": [per_unit * min(spread) / gbs_per_pct,
+                                                     per_unit * max(spread) / gbs_per_pct],
+                "dram_bw_util_pct": work["dram_bw_util_pct"],
+                "sm_util_pct": work["sm_util_pct"], "sm_occupancy_pct": work["sm_occupancy_pct"],
+                "fp32_util_pct": work["fp32_util_pct"], "calibration": cal,
+                "note": "NVML GPM counters (read-only), sampled twice while the device runs the timed "
+                        "region's schedule unprofiled; the DRAM percentage is converted to bytes with "
+                        "the copy's GB/s per percent (the range uses the fill's and the sum's)"}
+    finally:
+        lc.close()
+
+
 # ------------------------------------------------------------------------------------------
 # inputs
 # ------------------------------------------------------------------------------------------
@@ -640,6 +786,7 @@ def run_ours(args, rank, world, local_rank, dist):
         synchronisation on both sides; returns the slowest rank's milliseconds."""
         barrier()
         torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_push("timed_region")  # (a profiler can replay one region whole)
         e0.record(stream)
         for _, sth, _ in handles[1:]:
             sth.wait_event(e0)  # fork
@@ -652,6 +799,7 @@ def run_ours(args, rank, world, local_rank, dist):
             stream.wait_event(ev)  # join
         e1.record(stream)
         torch.cuda.synchronize(dev)
+        torch.cuda.nvtx.range_pop()
         barrier()
         return slowest(dist, e0.elapsed_time(e1))
 
@@ -666,6 +814,29 @@ def run_ours(args, rank, world, local_rank, dist):
         while len(blocks) < reps:
             blocks.append(timed_block())
     launches = (sum(h[0].kernel_launches() for h in handles) - l0) / len(blocks)
+
+    # live DRAM traffic and SM counters over the timed region's schedule (outside the timed
+    # regions): the same steps on the same handles and streams, forked and joined as above
+    live = None
+    if not args.no_live_counters:
+        def region():
+            e0.record(stream)
+            for _, sth, _ in handles[1:]:
+                sth.wait_event(e0)
+            for i in range(args.steps):
+                step(next_step[0] + i)
+            next_step[0] += args.steps
+            for _, sth, _ in handles[1:]:
+                ev = torch.cuda.Event()
+                ev.record(sth)
+                stream.wait_event(ev)
+        live = live_dram(torch, dev, local_rank, region, float(statistics.median(blocks)), args.steps,
+                         "integration")
+        if "dram_bytes_per_integration" in live:
+            # one pass over the packed input and one write of the spectra
+            alg = 4 * N_IF * WORDS_PER_IF + 4 * (autos.numel() + cross.numel() + stokes.numel())
+            live["algorithmic_bytes_per_integration"] = alg
+            live["traffic_over_algorithmic"] = live["dram_bytes_per_integration"] / alg
     for hd in handles[1:]:
         hd[0].close()
     t_max = float(statistics.median(blocks))
@@ -894,6 +1065,7 @@ def run_ours(args, rank, world, local_rank, dist):
         "repeats": spread["repeats"],
         "spread": spread,
         "clocks": clocks,
+        "live_counters": live,
         "pipeline": {"handles": H, "e2e_handles": None if args.no_e2e else max(2, args.e2e_handles),
                      "ctas_per_sm_caps": args.caps or "library default",
                      "note": "consecutive steps (independent 1-s integrations) alternate over this many "
@@ -1005,6 +1177,8 @@ def main():
                     help="segments per kernel pass (0: the library's default, sized to keep the slab in L2)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-live-counters", action="store_true",
+                    help="skip the NVML GPM pass (live DRAM bytes per integration, SM counters)")
     ap.add_argument("--no-variants", action="store_true", help="skip the overlap / code-statistics variants")
     ap.add_argument("--sweep", default="", help="comma-separated log2 N: print the throughput against N instead")
     ap.add_argument("--only", choices=["batch_graph", "tc_precision", "adjoint"], default=None,
