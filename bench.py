@@ -1174,7 +1174,7 @@ def main():
                     help="P1,P2: CTAs per SM of the two FFT kernels at most, for every handle of the timed and "
                          "end-to-end loops (0: as many as fit; empty: the library's choice)")
     ap.add_argument("--batch-segments", type=int, default=0,
-                    help="segments per kernel pass (0: the library's default, sized to keep the slab in L2)")
+                    help="segments per kernel pass (0: the library's default, at least 64 segments per pass)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-live-counters", action="store_true",
