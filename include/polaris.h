@@ -311,6 +311,9 @@ int polaris_power_from_histogram(int bits, const uint64_t* counts, double* momen
  *   grad_window, grad_gains, grad_leak   out: d loss / d (each real parameter), in the
  *                layouts of the inputs; all three or none.  The adjoint transforms every
  *                segment again instead of storing the spectra.
+ * Speed: for n_fft in [512, 16384] with packed[0], packed[1] and window 16-byte aligned
+ * (as every cudaMalloc or torch allocation is), the segment passes run kernels specialised
+ * per n_fft; other calls run kernels for any n_fft, with results equal within rounding.
  * Errors: POLARIS_EINVAL for bad arguments, POLARIS_ECUDA for a CUDA error (text from
  * polaris_adj_last_error; NULL handle: the last failed create in this thread). */
 typedef struct polaris_adj polaris_adj;

@@ -32,6 +32,8 @@
 //   k_adj_forward  a grid of G CTAs, each over segments b, b + G, ...: decode, window, a
 //                  radix-16 Stockham transform of the pair x + i y in shared memory, split
 //                  into X and Y, per-CTA partial sums of |X|^2, |Y|^2, X conj(Y)
+//                  (N = 2^9 .. 2^14: k_adjs_forward, the same per size at compile time,
+//                  polaris_adjoint_sized.cu; likewise k_adjs_window)
 //   k_adj_bins     per bin: partials summed (fp32 slices, added in fp64), the model,
 //                  Stokes and loss in fp64, the gain and leakage gradients and the
 //                  window-adjoint matrix in fp32
@@ -50,29 +52,11 @@
 #include <vector>
 
 #include "../../include/polaris.h"
-#include "polaris_device.cuh"
+#include "polaris_adjoint.cuh"
 
 namespace polaris {
 
 constexpr int kMaxCtasPerSm = 8;
-
-struct AdjArgs {
-  const uint32_t* in[2];  // the two IFs' packed words
-  int N, log2n, nbin, nseg, grid, threads;
-  const float2* tw;       // per-pass twiddles: tw[r Ns + k - 1] = W_{Ns R}^{r k} (N - 1 entries)
-  const float* window;    // N
-  float* part;            // [grid][4][nbin]: |X|^2, |Y|^2, Re X conj(Y), Im X conj(Y)
-  const float4* mat;      // per bin (m11, m12), (m21, m22)
-  float* gpart;           // [grid][N] window-gradient partials
-};
-
-// shared-memory layout of the N points: one float2 of padding after every 16 keeps the
-// stride-16 writes of the first pass, and every other access, free of bank conflicts
-__host__ __device__ __forceinline__ int apad(int i) { return i + (i >> 4); }
-__host__ __device__ constexpr int adj_smem_points(int N) { return N + N / 16; }
-
-__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 c_conj(float2 a) { return make_float2(a.x, -a.y); }
 
 // One Stockham autosort pass of radix R (Ns = product of the radices already applied), in
 // place in z: every j < N/R reads z[j + r N/R] (r < R), multiplies by W_{Ns R}^{r (j mod Ns)}
@@ -120,17 +104,6 @@ __device__ __forceinline__ void adj_fft(float2* z, int N, int log2n, const float
     case 2: stockham_pass<4>(z, N, Ns, tw, T); break;
     case 3: stockham_pass<8>(z, N, Ns, tw, T); break;
     default: break;
-  }
-}
-
-// level of sample idx of one IF
-template <int BITS>
-__device__ __forceinline__ float adj_level(const uint32_t* __restrict__ in, long long idx) {
-  if constexpr (BITS == 8) {
-    return (float)(int)__ldg(reinterpret_cast<const signed char*>(in) + idx);
-  } else {
-    constexpr int SPW = 32 / BITS;
-    return decode_level<BITS>(__ldg(in + idx / SPW), (uint32_t)(idx % SPW) * BITS);
   }
 }
 
@@ -383,6 +356,7 @@ using namespace polaris;
 
 struct polaris_adj {
   int N = 0, log2n = 0, nbin = 0, bits = 0, device = 0, threads = 0, grid_max = 0, bin_blocks = 0;
+  bool sized = false;  // the size-specialised segment kernels (polaris_adjoint_sized.cu)
   size_t smem = 0;
   float2* d_tw = nullptr;
   float* d_part = nullptr;   // [grid_max][4][nbin]
@@ -441,6 +415,7 @@ extern "C" int polaris_adj_create(int64_t n_fft, int bits, int device, polaris_a
   h->bits = bits;
   h->device = device;
   h->threads = h->N / 16;
+  h->sized = h->log2n >= kAdjSizedMin && h->log2n <= kAdjSizedMax;
   h->smem = (size_t)adj_smem_points(h->N) * sizeof(float2);
   h->bin_blocks = (h->nbin + kBinsPerBlock - 1) / kBinsPerBlock;
   int prev = 0;
@@ -448,6 +423,8 @@ extern "C" int polaris_adj_create(int64_t n_fft, int bits, int device, polaris_a
   cudaSetDevice(device);
   int nsm = 0, occ = 0;
   cudaError_t e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+  // the kernels for any N always (they also take calls whose buffers are not 16-byte
+  // aligned), the size-specialised ones where they exist; both run on the same grid
   if (e == cudaSuccess) {
     switch (bits) {
       case 1: e = adj_prepare<1>(h, &occ); break;
@@ -455,6 +432,11 @@ extern "C" int polaris_adj_create(int64_t n_fft, int bits, int device, polaris_a
       case 4: e = adj_prepare<4>(h, &occ); break;
       default: e = adj_prepare<8>(h, &occ); break;
     }
+  }
+  if (e == cudaSuccess && h->sized) {
+    int occ_sized = 0;
+    e = adj_sized_prepare(h->log2n, bits, &occ_sized);
+    occ = std::min(occ, occ_sized);
   }
   if (e != cudaSuccess || occ < 1) {
     cudaGetLastError();
@@ -516,7 +498,9 @@ static cudaError_t adj_segments(const AdjArgs& a, size_t smem, bool window_pass,
   return cudaGetLastError();
 }
 
-static cudaError_t adj_segments_bits(int bits, const AdjArgs& a, size_t smem, bool window_pass, cudaStream_t st) {
+static cudaError_t adj_segments_bits(int bits, const AdjArgs& a, size_t smem, bool window_pass, bool sized,
+                                     cudaStream_t st) {
+  if (sized) return adj_sized_launch(a.log2n, bits, window_pass, a, st);
   switch (bits) {
     case 1: return adj_segments<1>(a, smem, window_pass, st);
     case 2: return adj_segments<2>(a, smem, window_pass, st);
@@ -558,7 +542,10 @@ extern "C" int polaris_adj_run(polaris_adj* h, const void* const* packed, int64_
   a.part = h->d_part;
   a.mat = h->d_mat;
   a.gpart = h->d_gpart;
-  cudaError_t e = adj_segments_bits(h->bits, a, h->smem, false, st);
+  // the size-specialised kernels read the inputs and the window by 16-byte vector loads
+  auto aligned16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  const bool sized = h->sized && aligned16(packed[0]) && aligned16(packed[1]) && aligned16(window);
+  cudaError_t e = adj_segments_bits(h->bits, a, h->smem, false, sized, st);
   if (e == cudaSuccess) {
     BinArgs b;
     b.part = h->d_part;
@@ -579,7 +566,7 @@ extern "C" int polaris_adj_run(polaris_adj* h, const void* const* packed, int64_
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && grads) {
-    e = adj_segments_bits(h->bits, a, h->smem, true, st);
+    e = adj_segments_bits(h->bits, a, h->smem, true, sized, st);
     if (e == cudaSuccess) {
       k_adj_wsum<<<(h->N + kBinsPerBlock - 1) / kBinsPerBlock, kBinsPerBlock * kSlices, 0, st>>>(h->d_gpart, a.grid, h->N, grad_window);
       e = cudaGetLastError();

@@ -88,7 +88,10 @@ def _t(torch, x):
     return torch.from_numpy(np.ascontiguousarray(x)).cuda()
 
 
-@pytest.mark.parametrize("logn,bits,nseg", [(6, 8, 6), (10, 2, 12), (14, 8, 8)])
+# log2 N 6 runs the kernels for any N, 9..14 the size-specialised ones (every width; at 2^9
+# and 2^12 more segments than the grid has CTAs, so that each CTA sums several)
+@pytest.mark.parametrize("logn,bits,nseg", [(6, 8, 6), (9, 1, 1300), (10, 2, 12), (11, 4, 10), (12, 2, 500),
+                                            (13, 4, 5), (14, 8, 8), (14, 1, 3)])
 def test_forward_and_gradients_match_oracle(env, orc, logn, bits, nseg):
     torch, pol = env
     n_fft = 1 << logn
@@ -108,6 +111,35 @@ def test_forward_and_gradients_match_oracle(env, orc, logn, bits, nseg):
     for name, got, ref in (("window", r["grad_window"], gw_ref), ("gains", r["grad_gains"], gg_ref),
                            ("leak", r["grad_leak"], gd_ref)):
         _assert_grad(got.cpu().numpy(), ref, name)
+
+
+def test_unaligned_buffers_take_the_general_kernels(env, orc):
+    """The size-specialised kernels (2^9..2^14) read inputs and window by 16-byte vector loads;
+    a call whose buffers are not 16-byte aligned runs the kernels for any N instead, with the
+    same results within the bounds above."""
+    torch, pol = env
+    n_fft, bits, nseg = 4096, 2, 7
+    host, dev, n, w, g, d = _case(torch, n_fft, nseg, bits, 51)
+    st_ref, _ = orc.leak_forward(host, bits, n_fft, n, w, g, d)
+    target = (st_ref * 0.9).astype(np.float32)
+    gw_ref, gg_ref, gd_ref = orc.leak_grad(host, bits, n_fft, n, w, g, d, target)
+    # the same values one 4-byte element past a 16-byte boundary
+    w_off = torch.zeros(n_fft + 1, dtype=torch.float32, device="cuda")[1:]
+    w_off.copy_(_t(torch, w))
+    dev_off = []
+    for x in dev:
+        y = torch.zeros(x.numel() + 1, dtype=x.dtype, device="cuda")[1:]
+        y.copy_(x)
+        dev_off.append(y)
+    assert w_off.data_ptr() % 16 and all(y.data_ptr() % 16 for y in dev_off)
+    with pol.Adjoint(n_fft, bits) as adj:
+        for ins, win in ((dev, _t(torch, w)), (dev_off, w_off)):
+            r = adj.run(ins, n, win, _t(torch, g), _t(torch, d), _t(torch, target), grads=True)
+            torch.cuda.synchronize()
+            assert np.abs(r["stokes"].cpu().numpy() - st_ref).max() <= 1e-5 * np.abs(st_ref).max()
+            for name, got, ref in (("window", r["grad_window"], gw_ref), ("gains", r["grad_gains"], gg_ref),
+                                   ("leak", r["grad_leak"], gd_ref)):
+                _assert_grad(got.cpu().numpy(), ref, name)
 
 
 def test_autograd_wrapper_matches_direct_call(env):
