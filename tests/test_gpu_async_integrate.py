@@ -104,3 +104,58 @@ def test_feed_mode_is_checked(env):
         arr = (ctypes.c_void_p * 2)(words.ctypes.data, words.ctypes.data)
         rc = pol.load().spectrometer_feed(sp._h, arr, 1024, 3, None)
         assert rc == pol.EINVAL
+
+
+def test_async_host_feeds_on_many_streams(env, orc):
+    """Asynchronous host feeds on several streams: eight integrations of distinct data on four
+    handles and four streams, all queued before any is waited for, each against the oracle;
+    then the feeds of four of them captured into CUDA graphs (one per handle and stream),
+    replayed once and checked again."""
+    torch, pol = env
+    n_if, bits, n_fft, nseg, H, steps = 4, 2, 1 << 14, 5, 4, 8
+    pairs = [(0, 2), (1, 3)]
+    n = nseg * n_fft
+    rng = np.random.default_rng(99)
+    packed = [[synth.pack(synth.random_codes(rng, n, bits), bits) for _ in range(n_if)] for _ in range(steps)]
+    pinned = [[torch.from_numpy(p.view(np.int32)).pin_memory() for p in step] for step in packed]
+    host = [[t.numpy().view(np.uint32) for t in step] for step in pinned]
+    nb = n_fft // 2 + 1
+    outs = [_pinned_out(torch, n_if, len(pairs), nb) for _ in range(steps)]
+    streams = [torch.cuda.Stream() for _ in range(H)]
+    sps = [pol.Spectrometer(n_if, bits, n_fft) for _ in range(H)]
+
+    def check(i):
+        cr = outs[i]["cross"].numpy()
+        got = {"autos": outs[i]["autos"].numpy(), "cross": cr[..., 0] + 1j * cr[..., 1],
+               "stokes": outs[i]["stokes"].numpy()}
+        assert_close(got, orc.spectrometer(packed[i], bits, n_fft, n), pairs, 1e-5)
+
+    try:
+        torch.cuda.synchronize()
+        for i in range(steps):
+            sp, st = sps[i % H], streams[i % H]
+            sp.feed(host[i], n, on_device=False, stream=st, host_async=True)
+            assert sp.integrate_async(outs[i], stream=st) == nseg
+        torch.cuda.synchronize()
+        for i in range(steps):
+            check(i)
+        for o in outs:
+            for t in o.values():
+                t.fill_(7.0)
+        # captured: host-async feeds of the first H steps, one per handle on its own stream
+        graphs = []
+        for k in range(H):
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=streams[k]):
+                sps[k].feed(host[k], n, on_device=False, stream=streams[k], host_async=True)
+                sps[k].integrate_async(outs[k], stream=streams[k])
+            graphs.append(g)
+        torch.cuda.synchronize()
+        for g in graphs:
+            g.replay()
+        torch.cuda.synchronize()
+        for k in range(H):
+            check(k)
+    finally:
+        for sp in sps:
+            sp.close()
