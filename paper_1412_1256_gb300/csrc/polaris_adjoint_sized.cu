@@ -13,8 +13,8 @@
 //     memory once, at the end (instead of a read and a write per segment);
 //   - the twiddles of the passes with Ns <= 256 are a shared-memory copy of the host's table
 //     (exact FP64 values rounded once); the last pass of N >= 2^13 (Ns = 4096) forms
-//     W_N^j, j = t + q T, as W_N^t (from the table, once per thread) times the constant
-//     W_PPT^q, and W_N^{r j} as its powers.
+//     W_N^{r j}, j = t + q T, as W_N^{r t} (from the table, once per thread) times the
+//     constant W_PPT^{r q}: one rounding of two correctly rounded factors.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,6 +31,7 @@ struct AdjPlan {
   static constexpr int F = LOGN / 4, REM = LOGN % 4;     // F radix-16 passes, then one of radix 2^REM
   static constexpr int NS_LAST = 1 << (4 * F);           // Ns of that last pass
   static constexpr bool FLY = REM > 0 && NS_LAST > 256;  // its twiddles formed in registers
+  static constexpr int RW = (REM > 0 ? (1 << REM) : 2) - 1;  // W_N^{r t}, r = 1 .. radix - 1, per thread
   static constexpr int NTAB = FLY ? NS_LAST - 1 : N - 1; // twiddle-table entries in shared memory
   static constexpr int DATA = adj_smem_points(N);
   static constexpr int SLOTS = WARPS >= 4 ? WARPS / 4 : 1;  // warps sharing a tensor-memory lane quadrant
@@ -47,7 +48,8 @@ struct AdjPlan {
 // z[j + r N/R] (r < R), multiplies by W_{NS R}^{r (j mod NS)}, takes an R-point DFT and writes
 // output r to z[(j / NS) NS R + r NS + j mod NS].  All reads come before any write.
 template <int LOGN, int R, int NS>
-__device__ __forceinline__ void adjs_pass(float2* z, const float2* __restrict__ tws, float2 wt, int tid) {
+__device__ __forceinline__ void adjs_pass(float2* z, const float2* __restrict__ tws,
+                                          const float2 (&wt)[AdjPlan<LOGN>::RW], int tid) {
   using PL = AdjPlan<LOGN>;
   constexpr int T = PL::T, JPT = PL::PPT / R, M = PL::N / R;
   float2 v[JPT][R];
@@ -55,21 +57,20 @@ __device__ __forceinline__ void adjs_pass(float2* z, const float2* __restrict__ 
     constexpr int q = decltype(q_)::value;
     const int j = tid + q * T;
     const int k = j & (NS - 1);
-    float2 wj = wt, wr = make_float2(1.f, 0.f);
-    if constexpr (NS > 256 && q > 0) {  // W_N^j = W_N^t W_PPT^q (T = N/PPT)
-      constexpr ct::CS cs = ct::cossin2pi(q, PL::PPT);
-      wj = cmul(wt, make_float2((float)cs.c, (float)(-cs.s)));
-    }
     sfor<0, R>([&](auto r_) {
       constexpr int r = decltype(r_)::value;
       float2 x = z[apad(j + r * M)];
       if constexpr (NS > 1 && r > 0) {
         if constexpr (NS <= 256) {
           x = cmul(x, tws[r * NS + k - 1]);
-        } else {  // the last pass: k = j, W_N^{r j} = (W_N^j)^r
-          if constexpr (r == 1) wr = wj;
-          else wr = cmul(wr, wj);
-          x = cmul(x, wr);
+        } else {  // the last pass: k = j, W_N^{r j} = W_N^{r t} W_PPT^{r q} (T = N/PPT)
+          constexpr int e = (r * q) % PL::PPT;
+          float2 w = wt[r - 1];
+          if constexpr (e != 0) {
+            constexpr ct::CS cs = ct::cossin2pi(e, PL::PPT);
+            w = cmul(w, make_float2((float)cs.c, (float)(-cs.s)));
+          }
+          x = cmul(x, w);
         }
       }
       v[q][ct::bitrev(r, R)] = x;
@@ -92,7 +93,8 @@ __device__ __forceinline__ void adjs_pass(float2* z, const float2* __restrict__ 
 
 // forward DFT of the N points in z (natural order in and out); callers sync before
 template <int LOGN>
-__device__ __forceinline__ void adjs_fft(float2* z, const float2* __restrict__ tws, float2 wt, int tid) {
+__device__ __forceinline__ void adjs_fft(float2* z, const float2* __restrict__ tws,
+                                         const float2 (&wt)[AdjPlan<LOGN>::RW], int tid) {
   using PL = AdjPlan<LOGN>;
   sfor<0, PL::F>([&](auto p_) { adjs_pass<LOGN, 16, (1 << (4 * decltype(p_)::value))>(z, tws, wt, tid); });
   if constexpr (PL::REM > 0) adjs_pass<LOGN, (1 << PL::REM), PL::NS_LAST>(z, tws, wt, tid);
@@ -156,17 +158,19 @@ __device__ __forceinline__ void adjs_load(const AdjArgs& a, float2* z, long long
   });
 }
 
-// the set-up both kernels share: the twiddle table in shared memory, this thread's W_N^t for
-// a last pass formed in registers, and the CTA's tensor memory (this thread's COLS columns
+// the set-up both kernels share: the twiddle table in shared memory, this thread's W_N^{r t}
+// for a last pass formed in registers, and the CTA's tensor memory (this thread's COLS columns
 // zeroed); returns the address of those columns
 template <int LOGN, int TCOLS, int COLS>
-__device__ __forceinline__ uint32_t adjs_setup(const AdjArgs& a, float2* tws, uint32_t* tslot, float2& wt,
-                                               uint32_t& tbase, int tid) {
+__device__ __forceinline__ uint32_t adjs_setup(const AdjArgs& a, float2* tws, uint32_t* tslot,
+                                               float2 (&wt)[AdjPlan<LOGN>::RW], uint32_t& tbase, int tid) {
   using PL = AdjPlan<LOGN>;
   const int warp = tid >> 5;
   for (int i = tid; i < PL::NTAB; i += PL::T) tws[i] = __ldg(a.tw + i);
-  wt = make_float2(1.f, 0.f);
-  if constexpr (PL::FLY) wt = __ldg(a.tw + PL::NS_LAST + tid - 1);  // W_N^t (entry r = 1, k = t)
+  sfor<0, PL::RW>([&](auto r_) {  // W_N^{r t}: the table's entry r, k = t of the last pass
+    constexpr int r = decltype(r_)::value + 1;
+    wt[r - 1] = PL::FLY ? __ldg(a.tw + r * PL::NS_LAST + tid - 1) : make_float2(1.f, 0.f);
+  });
   tbase = cta_tmem_begin<TCOLS>(tslot, warp);  // (its barrier also publishes the table)
   const uint32_t tacc = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * COLS);
   float z16[16];
@@ -185,7 +189,7 @@ __global__ void __launch_bounds__(AdjPlan<LOGN>::T) k_adjs_forward(AdjArgs a) {
   float2* tws = zs + PL::DATA;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(tws + PL::NTAB);
   const int tid = threadIdx.x;
-  float2 wt;
+  float2 wt[PL::RW];
   uint32_t tbase;
   const uint32_t tacc = adjs_setup<LOGN, PL::TCOLS_F, PL::FCOLS>(a, tws, tslot, wt, tbase, tid);
 #pragma unroll 1
@@ -252,7 +256,7 @@ __global__ void __launch_bounds__(AdjPlan<LOGN>::T) k_adjs_window(AdjArgs a) {
   float2* tws = zs + PL::DATA;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(tws + PL::NTAB);
   const int tid = threadIdx.x;
-  float2 wt;
+  float2 wt[PL::RW];
   uint32_t tbase;
   const uint32_t tacc = adjs_setup<LOGN, PL::TCOLS_W, PL::WCOLS>(a, tws, tslot, wt, tbase, tid);
 #pragma unroll 1

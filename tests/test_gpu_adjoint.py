@@ -3,20 +3,22 @@ loss against the FP64 oracle, gradients against the oracle's FP64 gradient (itse
 central differences) element by element and against central differences of the FP64 oracle
 loss, and the torch.autograd wrapper against the direct call.
 
-Gradient bound, per element: |g - g_ref| <= 1e-3 |g_ref| + 1e-6 max|g_ref| (max over the
+Gradient bound, per element: |g - g_ref| <= 1e-3 |g_ref| + 4e-6 max|g_ref| (max over the
 gradient's family: window taps, gains or leakage terms).  The relative part is the 1e-3 the
 calibration asks for; the floor covers elements that nearly cancel.  An FP32 transform of
-log2 N <= 14 radix-2 stages carries a relative error of about log2 N * 2^-24 ~ 1e-6 per term
-(the measured median relative error of the gradients is 3e-7..1.5e-6), and an element that
-cancels sums terms no larger than its family's largest element, so its absolute error is
-about 1e-6 of that maximum (measured: at most 2.7e-7 of it)."""
+log2 N <= 14 radix-2 stages gives the spectral sums a relative error of up to about
+log2 N * 2^-24 = 8.3e-7; a leakage-gradient element adds four products of those sums
+(2a|gR|^2 B DR, 2a|gR|^2 C, c conj(gR) gL B, c conj(gR) gL DL C), none larger than its
+family's largest element, so one that cancels keeps up to about 4 x 8.3e-7 = 3.3e-6 of that
+maximum (measured: up to 2.0e-6 of it over 500-520 random segments at 2^14, with either
+kernel set; the median relative error of the gradients is 3e-7..1.5e-6)."""
 import numpy as np
 import pytest
 
 from paper_1412_1256_gb300 import synth
 
 pytestmark = pytest.mark.gpu
-REL, FLOOR = 1e-3, 1e-6
+REL, FLOOR = 1e-3, 4e-6
 
 
 def _assert_grad(got, ref, what):
@@ -140,6 +142,25 @@ def test_unaligned_buffers_take_the_general_kernels(env, orc):
             for name, got, ref in (("window", r["grad_window"], gw_ref), ("gains", r["grad_gains"], gg_ref),
                                    ("leak", r["grad_leak"], gd_ref)):
                 _assert_grad(got.cpu().numpy(), ref, name)
+
+
+def test_many_random_segments_2p14(env, orc):
+    """520 random 2-bit segments of 2^14 (each CTA sums three or four): the case that sets the
+    gradient floor above (near-cancelling leakage terms keep up to about 2e-6 of their
+    family's maximum)."""
+    torch, pol = env
+    n_fft, bits, nseg = 1 << 14, 2, 520
+    host, dev, n, w, g, d = _case(torch, n_fft, nseg, bits, 61)
+    st_ref, _ = orc.leak_forward(host, bits, n_fft, n, w, g, d)
+    target = (st_ref * 0.9).astype(np.float32)
+    gw_ref, gg_ref, gd_ref = orc.leak_grad(host, bits, n_fft, n, w, g, d, target)
+    with pol.Adjoint(n_fft, bits) as adj:
+        r = adj.run(dev, n, _t(torch, w), _t(torch, g), _t(torch, d), _t(torch, target), grads=True)
+        torch.cuda.synchronize()
+    assert np.abs(r["stokes"].cpu().numpy() - st_ref).max() <= 1e-5 * np.abs(st_ref).max()
+    for name, got, ref in (("window", r["grad_window"], gw_ref), ("gains", r["grad_gains"], gg_ref),
+                           ("leak", r["grad_leak"], gd_ref)):
+        _assert_grad(got.cpu().numpy(), ref, name)
 
 
 def test_autograd_wrapper_matches_direct_call(env):
