@@ -168,6 +168,20 @@ __device__ __forceinline__ float decode_level(uint32_t word, uint32_t shift) {
   }
 }
 
+// (a & b) | c and (a & b) ^ c as one three-input logic operation each (truth tables 0xEA and
+// 0x6A over the operand patterns 0xF0, 0xCC, 0xAA).  Written out because with two constant
+// operands the compiler spends two logic operations on each.
+__device__ __forceinline__ uint32_t and_or(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ uint32_t and_xor(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm("lop3.b32 %0, %1, %2, %3, 0x6A;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
 // The same decode from a rotation of the word, for a lane that decodes the same bit
 // offset of many words: with rot = decode_rot<BITS>(shift) computed once, a code sits at
 // bits [1, BITS] (b < 8) or [0, 8) (b = 8) of rotr(word, rot), so one funnel shift, one
@@ -180,9 +194,9 @@ template <int BITS>
 __device__ __forceinline__ float decode_level_rot(uint32_t word, uint32_t rot) {
   const uint32_t r = __funnelshift_r(word, word, rot);
   if constexpr (BITS == 8) {
-    return __uint_as_float((r & 0xFFu) ^ 0x4B000080u) - 8388736.0f;  // 2^23 + (c ^ 0x80) - 2^23 - 128
+    return __uint_as_float(and_xor(r, 0xFFu, 0x4B000080u)) - 8388736.0f;  // 2^23 + (c ^ 0x80) - 2^23 - 128
   } else {
-    return __uint_as_float((r & (((1u << BITS) - 1u) << 1)) | 0x4B000000u) - (8388608.0f + (float)((1 << BITS) - 1));
+    return __uint_as_float(and_or(r, ((1u << BITS) - 1u) << 1, 0x4B000000u)) - (8388608.0f + (float)((1 << BITS) - 1));
   }
 }
 
@@ -192,12 +206,13 @@ template <int BITS>
 __device__ __forceinline__ float2 decode_pair_rot(uint32_t wa, uint32_t wb, uint32_t rot) {
   const uint32_t ra = __funnelshift_r(wa, wa, rot), rb = __funnelshift_r(wb, wb, rot);
   if constexpr (BITS == 8) {
-    return __fadd2_rn(make_float2(__uint_as_float((ra & 0xFFu) ^ 0x4B000080u), __uint_as_float((rb & 0xFFu) ^ 0x4B000080u)),
+    return __fadd2_rn(make_float2(__uint_as_float(and_xor(ra, 0xFFu, 0x4B000080u)),
+                                  __uint_as_float(and_xor(rb, 0xFFu, 0x4B000080u))),
                       make_float2(-8388736.0f, -8388736.0f));
   } else {
     constexpr uint32_t m = ((1u << BITS) - 1u) << 1;
     constexpr float c = -(8388608.0f + (float)((1 << BITS) - 1));
-    return __fadd2_rn(make_float2(__uint_as_float((ra & m) | 0x4B000000u), __uint_as_float((rb & m) | 0x4B000000u)),
+    return __fadd2_rn(make_float2(__uint_as_float(and_or(ra, m, 0x4B000000u)), __uint_as_float(and_or(rb, m, 0x4B000000u))),
                       make_float2(c, c));
   }
 }
