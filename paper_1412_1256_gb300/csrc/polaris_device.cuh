@@ -380,8 +380,12 @@ struct Plan {
   static constexpr int REGION2 =
       (2 * UPW * LDE2 > 2 * UPW * (N2 + PADC)) ? 2 * UPW * LDE2 : 2 * UPW * (N2 + PADC);
   // W_N2^k at k + k/32.  (A lane-contiguous [q][p] table has fewer bank conflicts but
-  // measured slower in this kernel.)
-  static constexpr int TWT = N2 + N2 / 32 + 1;
+  // measured slower in this kernel.)  With one p per lane (PP = 1), W_N2^{q p} by (p, q) at
+  // p (Q2 + 1) + q instead: the lane's row, no index arithmetic per lookup, and rows of an odd
+  // number of 8-byte entries put a half-warp's 16 rows on distinct bank pairs.
+  static constexpr bool TWPQ = PP == 1;
+  static constexpr int LDT2 = Q2 + 1;
+  static constexpr int TWT = (TWPQ && P * LDT2 > N2 + N2 / 32 + 1) ? P * LDT2 : N2 + N2 / 32 + 1;
   static constexpr int TACC = ((2 * P + 15) / 16) * 16;    // tensor-memory columns per lane: accumulators
   static constexpr int TTW = ((2 * P + 15) / 16) * 16;     // and the lane's column twiddles W_N^{b u}
   static constexpr int TCOLS2 = pow2_at_least((WARPS / 4) * (TACC + TTW), 32);

@@ -830,7 +830,14 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
   const int so = (SL > 1) ? uw / UPS : 0;
   const int uoff = (SL > 1) ? uw % UPS : uw;
 
-  for (int k = tid; k < N2; k += PL::THREADS) tw2[k + (k >> 5)] = tw_small<N2>(k);
+  if constexpr (PL::TWPQ) {
+    for (int i = tid; i < P * Q2; i += PL::THREADS) {
+      const int pp = i / Q2, qq = i % Q2;
+      tw2[pp * PL::LDT2 + qq] = tw_small<N2>((qq * pp) & (N2 - 1));
+    }
+  } else {
+    for (int k = tid; k < N2; k += PL::THREADS) tw2[k + (k >> 5)] = tw_small<N2>(k);
+  }
   const uint32_t tbase = cta_tmem_begin<PL::TCOLS2>(tslot, warp);  // (its barrier also publishes tw2)
   // (pdl_wait -- the slab written by phase 1 and the accumulators cleared by the readout are
   // visible -- comes after the first item's tensor-memory set-up, which reads neither)
@@ -952,8 +959,12 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
           constexpr int q = decltype(q_)::value;
           float2 w = make_float2(1.f, 0.f);
           if constexpr (q > 0) {
-            const int k = (q * p) & (N2 - 1);
-            w = tw2[k + (k >> 5)];
+            if constexpr (PL::TWPQ) {
+              w = tw2[p * PL::LDT2 + q];
+            } else {
+              const int k = (q * p) & (N2 - 1);
+              w = tw2[k + (k >> 5)];
+            }
           }
           sfor<0, 2>([&](auto e_) {
             constexpr int e = decltype(e_)::value;
