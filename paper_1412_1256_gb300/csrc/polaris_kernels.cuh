@@ -380,7 +380,8 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
   static_assert(!JOINT || (N1 % BOXR == 0 && (BOXR * JC * 8) % 1024 == 0 && (size_t)N1 * JC * 8 <= PL::REGIONS1),
                 "joint output block");
   extern __shared__ __align__(1024) float2 sm1[];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // (warp index and tensor-memory base broadcast from lane 0: uniform registers, as in phase 2)
+  const int tid = threadIdx.x, warp = __shfl_sync(0xffffffffu, tid >> 5, 0), lane = tid & 31;
   if constexpr (JOINT) {
     // the swizzled joint block needs a 1024-byte aligned base (the declaration asks for it);
     // should that ever not hold, report and leave the work undone rather than misplace data
@@ -408,7 +409,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
 
   uint32_t tbase = 0, t_tw = 0;
   if constexpr (Q1 > 1) {
-    tbase = cta_tmem_begin<PL::TCOLS1>(tslot, warp);
+    tbase = __shfl_sync(0xffffffffu, cta_tmem_begin<PL::TCOLS1>(tslot, warp), 0);
     t_tw = tbase + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((warp >> 2) * PL::TW1);
     // this lane's twiddles W_N1^{q1 p}, p < P
     sfor<0, PL::TW1 / 16>([&](auto c_) {
@@ -767,7 +768,9 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
   constexpr int SL = PL::SL, UGW = PL::UGW, PP = PL::PP, NACC = PL::NACC;
   constexpr int LDQ = PL::LDQ2, LDE = PL::LDE2, TACC = PL::TACC;
   extern __shared__ float2 sm2[];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // (the warp index and the tensor-memory base broadcast from lane 0: values the compiler can
+  // keep in uniform registers, which the tensor-memory loads and stores address by)
+  const int tid = threadIdx.x, warp = __shfl_sync(0xffffffffu, tid >> 5, 0), lane = tid & 31;
   float2* region = sm2 + warp * PL::REGION2;
   float2* tw2 = sm2 + PL::WARPS * PL::REGION2;  // skewed table: W_N2^k at k + k/32
   uint32_t* tslot = reinterpret_cast<uint32_t*>(tw2 + PL::TWT);
@@ -838,7 +841,7 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
   } else {
     for (int k = tid; k < N2; k += PL::THREADS) tw2[k + (k >> 5)] = tw_small<N2>(k);
   }
-  const uint32_t tbase = cta_tmem_begin<PL::TCOLS2>(tslot, warp);  // (its barrier also publishes tw2)
+  const uint32_t tbase = __shfl_sync(0xffffffffu, cta_tmem_begin<PL::TCOLS2>(tslot, warp), 0);  // (its barrier also publishes tw2)
   // (pdl_wait -- the slab written by phase 1 and the accumulators cleared by the readout are
   // visible -- comes after the first item's tensor-memory set-up, which reads neither)
   bool waited = false;
