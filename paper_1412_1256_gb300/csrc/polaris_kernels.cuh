@@ -999,40 +999,57 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, 2) k_phase2(BatchArgs a, 
         }
         __syncwarp();
       }
-      // correlate into the tensor-memory accumulators
-      sfor<0, (NACC + 3) / 4>([&](auto c_) {
-        constexpr int cc = decltype(c_)::value;
-        float a16[16];
-        tmem_ld16(t_acc + 16 * cc, a16);
-        tmem_wait_ld();
-        if (act) {
-          sfor<0, 4>([&](auto k_) {
-            constexpr int slot = 4 * cc + decltype(k_)::value;
-            if constexpr (slot < NACC) {
-              constexpr int r = slot / Q2, m = slot % Q2;
-              float(&q)[4] = *reinterpret_cast<float(*)[4]>(a16 + 4 * (slot - 4 * cc));
-              if (!special) {
-                corr_acc(q, wv[r * Q2 + m], wv[(PP + r) * Q2 + m]);
-              } else {
-                const int d = j * PP + r + P * m;
-                float2 Uv, Vv;
-                if (d <= N2 / 2) {  // column 0: bins N1 d, mirror N1 (N2 - d)
-                  Uv = s0[d];
-                  const float2 t = s0[(N2 - d) & (N2 - 1)];
-                  Vv = make_float2(t.x, -t.y);
-                } else {  // column N1/2 at dh = d - N2/2 - 1: bins N1/2 + N1 dh, mirror N2 - 1 - dh
-                  const int dh = d - N2 / 2 - 1;
-                  Uv = sh[dh];
-                  const float2 t = sh[N2 - 1 - dh];
-                  Vv = make_float2(t.x, -t.y);
+      // correlate into the tensor-memory accumulators.  SP: this lane's unit is unit 0
+      // (column 0 and N1/2, from the mirror area); with one unit per warp and one segment per
+      // round that, and act, are the same for the whole warp and are decided once per segment.
+      auto correlate = [&](auto sp_) {
+        constexpr int SPK = decltype(sp_)::value;  // 0: not special, 1: special, 2: decided per lane
+        sfor<0, (NACC + 3) / 4>([&](auto c_) {
+          constexpr int cc = decltype(c_)::value;
+          float a16[16];
+          tmem_ld16(t_acc + 16 * cc, a16);
+          tmem_wait_ld();
+          if (act) {
+            sfor<0, 4>([&](auto k_) {
+              constexpr int slot = 4 * cc + decltype(k_)::value;
+              if constexpr (slot < NACC) {
+                constexpr int r = slot / Q2, m = slot % Q2;
+                float(&q)[4] = *reinterpret_cast<float(*)[4]>(a16 + 4 * (slot - 4 * cc));
+                auto special_bin = [&]() {
+                  const int d = j * PP + r + P * m;
+                  float2 Uv, Vv;
+                  if (d <= N2 / 2) {  // column 0: bins N1 d, mirror N1 (N2 - d)
+                    Uv = s0[d];
+                    const float2 t = s0[(N2 - d) & (N2 - 1)];
+                    Vv = make_float2(t.x, -t.y);
+                  } else {  // column N1/2 at dh = d - N2/2 - 1: bins N1/2 + N1 dh, mirror N2 - 1 - dh
+                    const int dh = d - N2 / 2 - 1;
+                    Uv = sh[dh];
+                    const float2 t = sh[N2 - 1 - dh];
+                    Vv = make_float2(t.x, -t.y);
+                  }
+                  corr_acc(q, Uv, Vv);
+                };
+                if constexpr (SPK == 0) {
+                  corr_acc(q, wv[r * Q2 + m], wv[(PP + r) * Q2 + m]);
+                } else if constexpr (SPK == 1) {
+                  special_bin();
+                } else {
+                  if (!special) corr_acc(q, wv[r * Q2 + m], wv[(PP + r) * Q2 + m]);
+                  else special_bin();
                 }
-                corr_acc(q, Uv, Vv);
               }
-            }
-          });
-        }
-        tmem_st16(t_acc + 16 * cc, a16);
-      });
+            });
+          }
+          tmem_st16(t_acc + 16 * cc, a16);
+        });
+      };
+      if constexpr (UPW == 1 && SL == 1) {
+        if (special) correlate(std::integral_constant<int, 1>{});
+        else correlate(std::integral_constant<int, 0>{});
+      } else {
+        correlate(std::integral_constant<int, 2>{});
+      }
       tmem_wait_st();
       if (act && special && j == 0) {  // the one extra bin: column N1/2 at dh = N2/2 - 1
         const float2 t = sh[N2 / 2];
