@@ -475,14 +475,20 @@ __global__ void __launch_bounds__(Plan<LOGN>::THREADS, Plan<LOGN>::MINB1)
         // TMA swizzle of that row width: 16-byte chunk k of row c sits at chunk k ^ (row
         // bits of the byte offset), so the 16 or 32 rows one store instruction writes fall
         // on distinct chunks
+        // Row c = C0 + q1 with C0 = r Q1 + P m a multiple of 8: the row bits the swizzle
+        // takes (bits 7-9 of the offset for 128-byte rows, 7-8 for 64-byte rows) are those
+        // of the lane's own first row, and C0's part of the offset has no bits below the
+        // ninth, so the swizzled offset is the lane's swizzled base plus C0's part.
+        static_assert(Q1 % 8 == 0 && P % 8 == 0, "joint block swizzle per lane");
         char* jb = reinterpret_cast<char*>(sm1);
+        const uint32_t jl = (uint32_t)((q1 * JC + warp * CW + cw) * 8);
+        char* jlane = jb + (jl ^ (((jl >> 7) & (uint32_t)ST::JSW) << 4));
         sfor<0, PQ>([&](auto r_) {
           constexpr int r = decltype(r_)::value;
           sfor<0, Q1>([&](auto m_) {
             constexpr int m = decltype(m_)::value;
-            uint32_t o = (uint32_t)(((r * Q1 + q1 + P * m) * JC + warp * CW + cw) * 8);
-            o ^= ((o >> 7) & (uint32_t)ST::JSW) << 4;
-            *reinterpret_cast<float2*>(jb + o) = slab_val(v[r * Q1 + m], r * Q1 + q1 + P * m);
+            *reinterpret_cast<float2*>(jlane + (r * Q1 + P * m) * JC * 8) =
+                slab_val(v[r * Q1 + m], r * Q1 + q1 + P * m);
           });
         });
         fence_async_shared();
