@@ -47,19 +47,27 @@ struct AdjPlan {
 // One Stockham pass of radix R with Ns = NS points already combined: every j < N/R reads
 // z[j + r N/R] (r < R), multiplies by W_{NS R}^{r (j mod NS)}, takes an R-point DFT and writes
 // output r to z[(j / NS) NS R + r NS + j mod NS].  All reads come before any write.
+// Every compile-time part of the indices below (q T, r M, r NS) is a multiple of 16, so
+// apad(x + c) = apad(x) + c + c/16: one padded base per lane and j, compile-time offsets.
+template <int C>
+__device__ __forceinline__ constexpr int apad_c() {
+  static_assert(C % 16 == 0, "offset of whole 16-point groups");
+  return C + C / 16;
+}
 template <int LOGN, int R, int NS>
 __device__ __forceinline__ void adjs_pass(float2* z, const float2* __restrict__ tws,
                                           const float2 (&wt)[AdjPlan<LOGN>::RW], int tid) {
   using PL = AdjPlan<LOGN>;
   constexpr int T = PL::T, JPT = PL::PPT / R, M = PL::N / R;
   float2 v[JPT][R];
+  const float2* zt = z + apad(tid);
   sfor<0, JPT>([&](auto q_) {
     constexpr int q = decltype(q_)::value;
     const int j = tid + q * T;
     const int k = j & (NS - 1);
     sfor<0, R>([&](auto r_) {
       constexpr int r = decltype(r_)::value;
-      float2 x = z[apad(j + r * M)];
+      float2 x = zt[apad_c<q * T + r * M>()];  // z[apad(j + r M)]
       if constexpr (NS > 1 && r > 0) {
         if constexpr (NS <= 256) {
           x = cmul(x, tws[r * NS + k - 1]);
@@ -80,13 +88,20 @@ __device__ __forceinline__ void adjs_pass(float2* z, const float2* __restrict__ 
   sfor<0, JPT>([&](auto q_) {
     constexpr int q = decltype(q_)::value;
     const int j = tid + q * T;
-    const int k = j & (NS - 1);
     dit<R>(v[q]);
-    const int base = (j - k) * R + k;
-    sfor<0, R>([&](auto r_) {
-      constexpr int r = decltype(r_)::value;
-      z[apad(base + r * NS)] = v[q][r];
-    });
+    if constexpr (NS == 1) {  // base = 16 j, outputs r < 16: apad(16 j + r) = 17 j + r
+      sfor<0, R>([&](auto r_) {
+        constexpr int r = decltype(r_)::value;
+        z[17 * j + r] = v[q][r];
+      });
+    } else {
+      const int k = j & (NS - 1);
+      float2* zb = z + apad((j - k) * R + k);
+      sfor<0, R>([&](auto r_) {
+        constexpr int r = decltype(r_)::value;
+        zb[apad_c<r * NS>()] = v[q][r];  // z[apad(base + r NS)]
+      });
+    }
   });
   __syncthreads();
 }
