@@ -101,9 +101,9 @@ struct ReadoutArgs {
 // consecutive bins per d: 128-byte lines per output array); a padded shared tile turns one
 // into the other.  The map k -> native slot is a bijection, so the block also clears the
 // slots it read: the accumulators start the next integration at zero without a memset.
-// Bins per block.  2048 bins (8 per thread) measured 51.6 us per 1-s integration at 2^17 in a
-// long three-handle pipeline against 53.0 us with 512, but the readout alone took 12.4 us
-// instead of 8.3 (a quarter of the blocks), which cost 4-9% of one handle's rate: 512 stays.
+// Bins per block.  At 2^17 with three integrations in flight, 1024 and 2048 bins (4 and 8 per
+// thread) ran at 613k and 601k Msample/s against 615k with 512; alone, the 2048-bin readout
+// took 12.1 us instead of 8.2 (a quarter of the blocks) and one handle's rate fell 6%.
 #ifndef POLARIS_READOUT_TILE
 #define POLARIS_READOUT_TILE 512
 #endif
