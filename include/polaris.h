@@ -314,6 +314,8 @@ int polaris_power_from_histogram(int bits, const uint64_t* counts, double* momen
  * Speed: for n_fft in [512, 16384] with packed[0], packed[1] and window 16-byte aligned
  * (as every cudaMalloc or torch allocation is), the segment passes run kernels specialised
  * per n_fft; other calls run kernels for any n_fft, with results equal within rounding.
+ * A handle's work buffers serve one run at a time: runs on one handle whose GPU work
+ * could overlap (on different streams) must be ordered by the caller.
  * Errors: POLARIS_EINVAL for bad arguments, POLARIS_ECUDA for a CUDA error (text from
  * polaris_adj_last_error; NULL handle: the last failed create in this thread). */
 typedef struct polaris_adj polaris_adj;

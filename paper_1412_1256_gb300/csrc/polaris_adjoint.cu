@@ -124,7 +124,7 @@ __device__ __forceinline__ void adj_load_segment(const AdjArgs& a, float2* z, lo
 template <int BITS>
 __device__ __forceinline__ void adj_forward_segment(const AdjArgs& a, float2* z, long long s, bool first) {
   const int N = a.N, nbin = a.nbin;
-  float* part = a.part + (size_t)blockIdx.x * 4 * nbin;
+  float4* part = a.part + (size_t)blockIdx.x * nbin;
   adj_load_segment<BITS>(a, z, s);
   __syncthreads();
   adj_fft(z, N, a.log2n, a.tw, a.threads);
@@ -134,10 +134,14 @@ __device__ __forceinline__ void adj_forward_segment(const AdjArgs& a, float2* z,
     const float2 Zk = z[apad(k)], Zm = c_conj(z[apad((N - k) & (N - 1))]);
     const float2 X = make_float2(0.5f * (Zk.x + Zm.x), 0.5f * (Zk.y + Zm.y));
     const float2 Y = make_float2(0.5f * (Zk.y - Zm.y), -0.5f * (Zk.x - Zm.x));
-    float v[4] = {fmaf(X.x, X.x, X.y * X.y), fmaf(Y.x, Y.x, Y.y * Y.y), fmaf(X.x, Y.x, X.y * Y.y),
-                  fmaf(X.y, Y.x, -X.x * Y.y)};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) part[q * nbin + k] = first ? v[q] : part[q * nbin + k] + v[q];
+    const float4 v = make_float4(fmaf(X.x, X.x, X.y * X.y), fmaf(Y.x, Y.x, Y.y * Y.y), fmaf(X.x, Y.x, X.y * Y.y),
+                                fmaf(X.y, Y.x, -X.x * Y.y));
+    if (first) {
+      part[k] = v;
+    } else {
+      const float4 o = part[k];
+      part[k] = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+    }
   }
   __syncthreads();
 }
@@ -210,7 +214,7 @@ __device__ __forceinline__ float2 fscale(float2 a, float s) { return make_float2
 __device__ __forceinline__ float fnorm(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
 
 struct BinArgs {
-  const float* part;
+  const float4* part;
   int grid, nbin;
   const float* gains;
   const float* leak;
@@ -222,9 +226,10 @@ struct BinArgs {
 };
 
 // A block covers kBinsPerBlock bins; its kSlices warps sum the per-CTA partials of the
-// segment kernel over interleaved slices of CTAs in fp32 (many loads in flight), the slice
-// sums are added in fp64 in slice order, then one warp evaluates the model per bin: the
-// sums, Stokes and loss in fp64, the gradients and the window-adjoint matrix in fp32.
+// segment kernel (one 16-byte load per CTA and bin) over interleaved slices of CTAs in fp32
+// (many loads in flight), the slice sums are added in fp64 in slice order, then one warp
+// evaluates the model per bin: the sums, Stokes and loss in fp64, the gradients and the
+// window-adjoint matrix in fp32.
 constexpr int kBinsPerBlock = 32, kSlices = 8;
 
 __global__ void __launch_bounds__(kBinsPerBlock * kSlices) k_adj_bins(BinArgs a) {
@@ -234,11 +239,13 @@ __global__ void __launch_bounds__(kBinsPerBlock * kSlices) k_adj_bins(BinArgs a)
   const int k = blockIdx.x * kBinsPerBlock + lane;
   float s4[4] = {0.f, 0.f, 0.f, 0.f};
   if (k < nbin) {
-#pragma unroll 4
+#pragma unroll 8
     for (int g = sl; g < a.grid; g += kSlices) {
-      const float* p = a.part + (size_t)g * 4 * nbin + k;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) s4[q] += __ldcg(p + q * nbin);
+      const float4 v = __ldcg(a.part + (size_t)g * nbin + k);
+      s4[0] += v.x;
+      s4[1] += v.y;
+      s4[2] += v.z;
+      s4[3] += v.w;
     }
   }
 #pragma unroll
@@ -316,6 +323,8 @@ __global__ void __launch_bounds__(kBinsPerBlock * kSlices) k_adj_bins(BinArgs a)
 }
 
 // five warps, one per quantity: block partials summed lane-strided, then across the warp
+// (the last block of k_adj_bins to finish doing this instead, elected by an atomic ticket
+// after a memory fence, measured slower: 20.6 us against 13.4 + 3.7 us)
 __global__ void __launch_bounds__(160) k_adj_finish(const double* bpart, int blocks, double* loss, float* grad_gains) {
   const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double t = 0.0;
@@ -331,6 +340,8 @@ __global__ void __launch_bounds__(160) k_adj_finish(const double* bpart, int blo
 }
 
 // window-gradient partials summed per tap: 32 taps per block, kSlices warps over the CTAs
+// (four taps per lane with one 16-byte load per CTA ran slower: 9.7 against 7.4 us, a
+// quarter of the blocks)
 __global__ void __launch_bounds__(kBinsPerBlock * kSlices) k_adj_wsum(const float* gpart, int grid, int N,
                                                                       float* grad_w) {
   __shared__ float red[kSlices][kBinsPerBlock];
@@ -359,7 +370,7 @@ struct polaris_adj {
   bool sized = false;  // the size-specialised segment kernels (polaris_adjoint_sized.cu)
   size_t smem = 0;
   float2* d_tw = nullptr;
-  float* d_part = nullptr;   // [grid_max][4][nbin]
+  float4* d_part = nullptr;  // [grid_max][nbin]
   float* d_gpart = nullptr;  // [grid_max][N]
   float4* d_mat = nullptr;   // [nbin][2]
   double* d_bpart = nullptr; // [bin_blocks][5]
@@ -460,7 +471,7 @@ extern "C" int polaris_adj_create(int64_t n_fft, int bits, int device, polaris_a
     Ns *= R;
   }
   bool ok = cudaMalloc((void**)&h->d_tw, tw.size() * sizeof(float2)) == cudaSuccess &&
-            cudaMalloc((void**)&h->d_part, (size_t)h->grid_max * 4 * h->nbin * sizeof(float)) == cudaSuccess &&
+            cudaMalloc((void**)&h->d_part, (size_t)h->grid_max * h->nbin * sizeof(float4)) == cudaSuccess &&
             cudaMalloc((void**)&h->d_gpart, (size_t)h->grid_max * h->N * sizeof(float)) == cudaSuccess &&
             cudaMalloc((void**)&h->d_mat, (size_t)h->nbin * 2 * sizeof(float4)) == cudaSuccess &&
             cudaMalloc((void**)&h->d_bpart, (size_t)h->bin_blocks * 5 * sizeof(double)) == cudaSuccess &&

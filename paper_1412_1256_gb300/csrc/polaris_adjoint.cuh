@@ -17,7 +17,7 @@ struct AdjArgs {
   int N, log2n, nbin, nseg, grid, threads;
   const float2* tw;       // per-pass twiddles: tw[r Ns + k - 1] = W_{Ns R}^{r k} (N - 1 entries)
   const float* window;    // N
-  float* part;            // [grid][4][nbin]: |X|^2, |Y|^2, Re X conj(Y), Im X conj(Y)
+  float4* part;           // [grid][nbin]: (|X|^2, |Y|^2, Re X conj(Y), Im X conj(Y)) per bin
   const float4* mat;      // per bin (m11, m12), (m21, m22)
   float* gpart;           // [grid][N] window-gradient partials
 };

@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(AdjPlan<LOGN>::T) k_adjs_forward(AdjArgs a) {
     tmem_wait_st();
     __syncthreads();  // z is refilled by the next segment
   }
-  float* part = a.part + (size_t)blockIdx.x * 4 * PL::NBIN;
+  float4* part = a.part + (size_t)blockIdx.x * PL::NBIN;
   sfor<0, PL::FCOLS / 16>([&](auto c_) {
     constexpr int cc = decltype(c_)::value;
     float acc[16];
@@ -251,10 +251,8 @@ __global__ void __launch_bounds__(AdjPlan<LOGN>::T) k_adjs_forward(AdjArgs a) {
       if constexpr (i < PL::BPT) {
         if (i < PL::BPT - 1 || tid == 0) {
           const int k = i < PL::BPT - 1 ? tid + T * i : N / 2;
-          sfor<0, 4>([&](auto q_) {
-            constexpr int q = decltype(q_)::value;
-            part[q * PL::NBIN + k] = acc[4 * (i - 4 * cc) + q];
-          });
+          constexpr int o = 4 * (i - 4 * cc);
+          part[k] = make_float4(acc[o], acc[o + 1], acc[o + 2], acc[o + 3]);
         }
       }
     });

@@ -115,6 +115,56 @@ def test_forward_and_gradients_match_oracle(env, orc, logn, bits, nseg):
         _assert_grad(got.cpu().numpy(), ref, name)
 
 
+def test_every_run_writes_loss_and_gain_gradients(env, orc):
+    """A sequence of runs on one handle (loss only, Stokes only, with gradients twice, loss
+    only) writes the loss and the gain gradients on every run that asks for them, into
+    outputs that start as NaN, and no loss on the run that does not: bitwise equal from run
+    to run (every sum has a fixed order) and equal to the oracle's."""
+    import ctypes
+
+    torch, pol = env
+    n_fft, nseg, bits = 1 << 12, 40, 2
+    host, dev, n, w, g, d = _case(torch, n_fft, nseg, bits, 77)
+    st_ref, _ = orc.leak_forward(host, bits, n_fft, n, w, g, d)
+    target = (st_ref * 0.95).astype(np.float32)
+    _, loss_ref = orc.leak_forward(host, bits, n_fft, n, w, g, d, target)
+    _, gg_ref, _ = orc.leak_grad(host, bits, n_fft, n, w, g, d, target)
+    lib = pol.load()
+    nb = n_fft // 2 + 1
+    W, G, D, T = (_t(torch, x) for x in (w, g, d, target))
+    arr = (ctypes.c_void_p * 2)(*[p.data_ptr() for p in dev])
+    nan = float("nan")
+    losses, gains = [], []
+    with pol.Adjoint(n_fft, bits) as adj:
+        for kind in ("loss", "stokes", "grads", "grads", "loss"):
+            st = torch.full((4, nb), nan, device="cuda")
+            loss = torch.full((1,), nan, dtype=torch.float64, device="cuda")
+            gw = torch.full((n_fft,), nan, device="cuda")
+            gg = torch.full((4,), nan, device="cuda")
+            gd = torch.full((2, nb, 2), nan, device="cuda")
+            grads = kind == "grads"
+            rc = lib.polaris_adj_run(adj._h, arr, n, W.data_ptr(), G.data_ptr(), D.data_ptr(),
+                                     None if kind == "stokes" else T.data_ptr(), st.data_ptr(),
+                                     None if kind == "stokes" else loss.data_ptr(),
+                                     gw.data_ptr() if grads else None, gg.data_ptr() if grads else None,
+                                     gd.data_ptr() if grads else None, None)
+            assert rc == 0
+            torch.cuda.synchronize()
+            assert torch.isfinite(st).all(), kind
+            if kind == "stokes":
+                assert torch.isnan(loss).all()  # not requested, not written
+                continue
+            losses.append(loss.cpu().numpy().copy())
+            assert np.isfinite(losses[-1]).all(), kind
+            if grads:
+                gains.append(gg.cpu().numpy().copy())
+                assert np.isfinite(gains[-1]).all()
+    assert all(x.tobytes() == losses[0].tobytes() for x in losses)
+    assert gains[0].tobytes() == gains[1].tobytes()
+    assert float(losses[0][0]) == pytest.approx(loss_ref, rel=1e-3)
+    _assert_grad(gains[0], gg_ref, "gains")
+
+
 def test_unaligned_buffers_take_the_general_kernels(env, orc):
     """The size-specialised kernels (2^9..2^14) read inputs and window by 16-byte vector loads;
     a call whose buffers are not 16-byte aligned runs the kernels for any N instead, with the
