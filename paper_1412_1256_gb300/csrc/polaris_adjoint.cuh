@@ -42,12 +42,11 @@ __device__ __forceinline__ float adj_level(const uint32_t* __restrict__ in, long
 }
 
 // Size-specialised segment kernels (polaris_adjoint_sized.cu) for log2 N in
-// [kAdjSizedMin, kAdjSizedMax].  adj_sized_smem: dynamic shared memory per CTA;
-// adj_sized_prepare: sets the kernels' shared-memory limit for this device (current) and
-// returns how many CTAs of the pair may share an SM (occupancy and tensor memory);
-// adj_sized_launch: one segment kernel (forward or window pass) on a.grid CTAs.
+// [kAdjSizedMin, kAdjSizedMax].  adj_sized_prepare: sets the kernels' shared-memory limit
+// for this device (current) and returns how many CTAs of the pair may share an SM
+// (occupancy and tensor memory); adj_sized_launch: one segment kernel (forward or window
+// pass) on a.grid CTAs.
 constexpr int kAdjSizedMin = 9, kAdjSizedMax = 14;
-size_t adj_sized_smem(int log2n);
 cudaError_t adj_sized_prepare(int log2n, int bits, int* ctas_per_sm);
 cudaError_t adj_sized_launch(int log2n, int bits, bool window_pass, const AdjArgs& a, cudaStream_t st);
 

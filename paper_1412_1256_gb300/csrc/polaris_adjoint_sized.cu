@@ -387,18 +387,6 @@ static cudaError_t adjs_any(int log2n, int bits, bool prepare, int* occ, bool wi
   }
 }
 
-size_t adj_sized_smem(int log2n) {
-  switch (log2n) {
-    case 9: return AdjPlan<9>::SMEM;
-    case 10: return AdjPlan<10>::SMEM;
-    case 11: return AdjPlan<11>::SMEM;
-    case 12: return AdjPlan<12>::SMEM;
-    case 13: return AdjPlan<13>::SMEM;
-    case 14: return AdjPlan<14>::SMEM;
-    default: return 0;
-  }
-}
-
 cudaError_t adj_sized_prepare(int log2n, int bits, int* ctas_per_sm) {
   return adjs_any(log2n, bits, true, ctas_per_sm, false, nullptr, nullptr);
 }
