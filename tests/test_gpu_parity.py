@@ -135,6 +135,40 @@ def test_overlap_and_ragged_feeds(pol, orc):
     assert_close(got, ref, [(0, 2), (1, 3)], TOL)
 
 
+@pytest.mark.parametrize("logn,bits,codes,nseg", [(17, 2, [0, 1, 2, 3], 3), (20, 8, [0x80, 0x7F], 2)])
+def test_constant_streams_closed_form(pol, orc, logn, bits, codes, nseg):
+    """Degenerate input at the benchmark's transform size (2^17 points, 2-bit, four IFs) and at
+    the largest (2^20, 8-bit, the extreme levels -128 and 127): every sample of IF i is the same
+    code, i.e. the constant level L_i, fed in two pieces with an empty feed between them.  With
+    a rectangular window each segment's spectrum is N L_i at bin 0 and zero elsewhere, so over
+    S segments autos[i][0] = S (N L_i)^2 and cross[p][0] = S N^2 L_a L_b (real), every other
+    bin vanishes (a transform of a constant meets only exact zeros off bin 0), and the Stokes
+    of bin 0 are Eq. (2) of those sums."""
+    n_fft = 1 << logn
+    n = n_fft * nseg
+    packed = [synth.pack(np.full(n, c), bits) for c in codes]
+    levels = [float(orc.decode(bits, p[:1], 1)[0]) for p in packed]
+    assert levels[0] != levels[-1]
+    half = n // 2
+    got = _run(pol, packed, bits, n_fft, n, chunks=[half, 0, n - half])
+    assert got["n_segments"] == nseg
+    for i, L in enumerate(levels):
+        a, a0 = got["autos"][i].astype(np.float64), nseg * (n_fft * L) ** 2
+        assert abs(a[0] - a0) <= 1e-6 * a0, i
+        assert np.abs(a[1:]).max() <= 1e-9 * a0, i
+    for p, (ia, ib) in enumerate(orc.default_pairs(len(codes))):
+        c = got["cross"][p].astype(np.complex128)
+        c0 = nseg * n_fft**2 * levels[ia] * levels[ib]
+        assert abs(c[0] - c0) <= 1e-6 * abs(c0), p
+        assert np.abs(c[1:]).max() <= 1e-9 * abs(c0), p
+        st_ref = orc.stokes(np.array([nseg * (n_fft * levels[ia]) ** 2]), np.array([nseg * (n_fft * levels[ib]) ** 2]),
+                            np.array([c0 + 0j]))
+        st = got["stokes"][p].astype(np.float64)
+        scale = np.abs(st_ref).max()
+        assert np.abs(st[:, 0] - st_ref[:, 0]).max() <= 1e-6 * scale, p
+        assert np.abs(st[:, 1:]).max() <= 1e-9 * scale, p
+
+
 def test_custom_taps_fp64_accum(pol, orc):
     n_fft, nseg = 16384, 12
     n = n_fft * nseg
